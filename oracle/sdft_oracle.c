@@ -90,6 +90,25 @@ static int64_t bit_reverse(int64_t n, int m) {
     return r;
 }
 
+/* cos and sin of 2 pi r / n.  At quarter turns (4r divisible by n) the
+ * entries c_{k,n}, s_{k,n} of Eq. (3) and the omega^(i,q) blocks are exactly
+ * 0 and +-1; they are returned exactly there (libm's sin(pi) is 1.2e-16, not
+ * 0) and taken from libm cos/sin everywhere else. */
+static void cos_sin_turn(int64_t r, int64_t n, double* c, double* s) {
+    r %= n;
+    if ((4 * r) % n == 0) {
+        static const double C[4] = {1.0, 0.0, -1.0, 0.0};
+        static const double S[4] = {0.0, 1.0, 0.0, -1.0};
+        int q = (int)((4 * r) / n) & 3;
+        *c = C[q];
+        *s = S[q];
+        return;
+    }
+    double ang = TWO_PI * (double)r / (double)n;
+    *c = cos(ang);
+    *s = sin(ang);
+}
+
 /* ------------------------------------------------------------------ O1 -- */
 /* One bin of Eq. (3): y_k^r = sum_n (x_n^r c_{k,n} + x_n^i s_{k,n}),
  *                     y_k^i = sum_n (x_n^i c_{k,n} - x_n^r s_{k,n}),
@@ -101,8 +120,8 @@ static void direct_bin(int64_t n, int64_t k, const double* xr, const double* xi,
     double acc_r = 0.0, acc_i = 0.0;
     for (int64_t t = 0; t < n; ++t) {
         int64_t r = (k * t) % n;
-        double ang = TWO_PI * (double)r / (double)n;
-        double c = cos(ang), s = sin(ang);
+        double c, s;
+        cos_sin_turn(r, n, &c, &s);
 #if SDFT_ORACLE_MUTATION == 1
         s = -s;                               /* planted: wrong sign of S */
 #endif
@@ -177,8 +196,8 @@ static void apply_W(int m, int i, double* v) {
 /* omega^(i,q) = [cos t  sin t; -sin t  cos t], t = 2 pi q / 2^i, applied to the
  * column (a, b); transpose != 0 applies its transpose [cos -sin; sin cos]. */
 static void apply_omega(int i, int64_t q, double* pair, int transpose) {
-    double t = TWO_PI * (double)q / (double)((int64_t)1 << i);
-    double c = cos(t), s = sin(t);
+    double c, s;
+    cos_sin_turn(q, (int64_t)1 << i, &c, &s);
 #if SDFT_ORACLE_MUTATION == 2
     s = -s;                                   /* planted: conjugated twiddle */
 #endif
@@ -334,8 +353,8 @@ int sdft_oracle_adjoint_direct(int64_t n, int64_t batch, const double* xr, const
             double acc_r = 0.0, acc_i = 0.0;
             for (int64_t t = 0; t < n; ++t) {
                 int64_t r = (k * t) % n;
-                double ang = TWO_PI * (double)r / (double)n;
-                double c = cos(ang), s = sin(ang);
+                double c, s;
+                cos_sin_turn(r, n, &c, &s);
 #if SDFT_ORACLE_MUTATION == 5
                 s = -s;                       /* planted: forward, not transpose */
 #endif

@@ -202,8 +202,8 @@ def pin_invariants(fn, sizes, tol=1e-12):
 
 
 def pin_integer_bins(fn, sizes):
-    """Integer inputs: bins 0, N/4, N/2, 3N/4 are exact integer sums whose
-    kernels are 1, (-j)^t, (-1)^t, (+j)^t."""
+    """Integer inputs: bins 0, N/4, N/2, 3N/4 are integer sums whose kernels
+    are 1, (-j)^t, (-1)^t, (+j)^t; they must come out exactly."""
     rng = np.random.default_rng(5)
     for n in sizes:
         xr = rng.integers(-8, 9, size=n).astype(float)
@@ -217,8 +217,8 @@ def pin_integer_bins(fn, sizes):
             kernels[3 * n // 4] = (1j) ** t
         for k, ker in kernels.items():
             exact = np.sum(x * np.round(ker.real) + x * 1j * np.round(ker.imag))
-            assert abs(yr[k] - exact.real) < 1e-9 and abs(yi[k] - exact.imag) < 1e-9, \
-                f"integer bin k={k} N={n}"
+            # exactly: every term is an integer times 0 or +-1
+            assert yr[k] == exact.real and yi[k] == exact.imag, f"integer bin k={k} N={n}"
 
 
 # ------------------------------------------------------ Kronecker form --
