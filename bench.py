@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the planar split-complex DFT on GB300.
+
+One step = one forward transform (Eq. (1) in the split form of Eq. (3)) of a
+whole synthetic batch, already resident in HBM: N = 1024, batch 65536, FP32
+planar, iid N(0, 1) from seed 1 (256 MiB per plane; each step reads 512 MiB
+and writes 512 MiB, more than L2, so no L2 flush is needed between steps).
+
+Prints ONE JSON line (rank 0):
+  value        Gpoints/s of the forward kernel over all ranks (B*N*ranks / time)
+  roofline     HBM roofline of that kernel: 16 algorithmic bytes per point
+               (read xr, xi; write yr, yi) / average launch time, against the
+               measured copy bandwidth of this GPU model
+  adjoint      the same for the adjoint kernel (E_2N^T)
+  e2e          the forward through the C ABI on pinned HOST buffers
+               (host->device, transform, device->host inside the timed region)
+  cpu_baseline the CPU oracle (Eq. (6) procedure, float64) on the host cores,
+               timed on a bounded sample of the same workload
+  clocks       SM clock and throttle reasons sampled during the timed region
+
+--impl reference times the CPU oracle instead (the only other implementation
+of the method that exists), on the same workload and metric.
+Multi-GPU (torchrun): every rank transforms its own batch (weak scaling); the
+transforms are independent, so there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "planar DFT Gpts/s & %HBM peak, N=1024 B=65536: FP32 vs split-BF16, fwd+adj"
+UNIT = "Gpts/s"
+N_POINTS = 1024
+BATCH = 65536
+BYTES_PER_POINT = 16          # algorithmic: 4 B each of xr, xi read and yr, yi written
+
+# DRAM bytes per launch of the timed kernels, from one ncu capture each
+# (profiles/), keyed by a hash of the kernel sources they were taken on; a
+# kernel changed since then reports traffic null.
+NCU_TRAFFIC = {}
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2504_07264_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def _peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "50"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def mark(self):
+        return len(self.lines)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self._t is not None:
+            self._t.join(timeout=2)
+
+    def summary(self, start: int = 0, end: int | None = None) -> dict:
+        rows = []
+        for ln in self.lines[start:end]:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                rows.append((float(p[0]), float(p[1]), p[4], p[5], p[6], p[7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------- CPU oracle --
+def cpu_oracle_rate(target_s: float = 10.0, max_batch: int = BATCH) -> dict:
+    """Time the CPU oracle's Eq. (6) procedure (float64, OpenMP over
+    transforms, all host cores) on a bounded sample of the workload."""
+    import numpy as np
+
+    import workloads
+    from oracle import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    used = oracle.thread_count(threads)
+    # calibrate on a small sample, then size the timed sample to ~target_s
+    cal = min(max_batch, max(64, 4 * used))
+    xr, xi = workloads.normal_planes(N_POINTS, cal, seed=1)
+    xr64, xi64 = xr.astype(np.float64), xi.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.dft_factored_dit(xr64, xi64, threads=used)
+    dt = time.perf_counter() - t0
+    per = dt / cal
+    sample = int(min(max_batch, max(cal, target_s / max(per, 1e-9))))
+    xr, xi = workloads.normal_planes(N_POINTS, sample, seed=1)
+    xr64, xi64 = xr.astype(np.float64), xi.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.dft_factored_dit(xr64, xi64, threads=used)
+    dt = time.perf_counter() - t0
+    return {"value": sample * N_POINTS / dt / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"first {sample} of the {BATCH} transforms (N={N_POINTS}, seed 1), "
+                      f"Eq. (6) procedure in float64, {dt:.1f} s"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import workloads
+    from oracle import oracle
+    oracle.build()
+    used = oracle.thread_count(os.cpu_count() or 1)
+    # size each step so that warmup + steps take a few minutes at most
+    cal = 256
+    xr, xi = workloads.normal_planes(N_POINTS, cal, seed=1)
+    t0 = time.perf_counter()
+    oracle.dft_factored_dit(xr.astype(np.float64), xi.astype(np.float64), threads=used)
+    per = (time.perf_counter() - t0) / cal
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    sample = int(max(16, min(BATCH, budget / max(per, 1e-9))))
+    xr, xi = workloads.normal_planes(N_POINTS, sample, seed=1)
+    xr64, xi64 = xr.astype(np.float64), xi.astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.dft_factored_dit(xr64, xi64, threads=used)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.dft_factored_dit(xr64, xi64, threads=used)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = sample * N_POINTS / dt / 1e9
+    desc = (f"{sample} of the {BATCH} transforms (N={N_POINTS}, seed 1) per step, "
+            f"Eq. (6) procedure in float64")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"bandwidth: N={N_POINTS} x {BATCH} planar, iid N(0,1) seed 1 "
+                               f"(CPU oracle on a bounded sample)", "n": N_POINTS, "batch": BATCH},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------ GPU arm --
+def _time_steps(fn, steps: int, stream) -> float:
+    """Milliseconds per step over `steps` calls, CUDA events on `stream`."""
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / steps
+
+
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2504_07264_gb300 import SDFT_ADJOINT, SDFT_FORWARD, Plan
+    from paper_2504_07264_gb300 import build as cuda_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cuda_build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    xr_h, xi_h = workloads.bandwidth()
+    points = N_POINTS * BATCH
+    xr = torch.from_numpy(xr_h).cuda()
+    xi = torch.from_numpy(xi_h).cuda()
+    yr = torch.empty_like(xr)
+    yi = torch.empty_like(xi)
+    plan = Plan(N_POINTS, BATCH)
+    launches_per_step = plan.launches(SDFT_FORWARD)
+
+    fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
+    adj = lambda: plan.execute(SDFT_ADJOINT, xr, xi, yr, yi, stream)  # noqa: E731
+    for _ in range(args.warmup):
+        fwd()
+        adj()
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = None
+    with ClockSampler(gpu_id if rank == 0 else None) as clk:
+        barrier()
+        m0 = clk.mark()
+        ms_fwd = _time_steps(fwd, args.steps, stream)
+        m1 = clk.mark()
+        barrier()
+        ms_adj = _time_steps(adj, args.steps, stream)
+        barrier()
+        # practical ceiling: a same-shape planar copy (both planes)
+        copy = lambda: (yr.copy_(xr), yi.copy_(xi))  # noqa: E731
+        for _ in range(3):
+            copy()
+        ms_copy = _time_steps(copy, max(10, args.steps // 4), stream)
+    clocks = clk.summary(m0, m1 if m1 > m0 else None)
+    if dist is not None:
+        t = torch.tensor([ms_fwd, ms_adj], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_fwd, ms_adj = t.tolist()
+
+    # end to end through the C ABI on pinned host buffers
+    hxr = torch.from_numpy(xr_h).pin_memory()
+    hxi = torch.from_numpy(xi_h).pin_memory()
+    hyr = torch.empty_like(hxr).pin_memory()
+    hyi = torch.empty_like(hxi).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)   # allocates staging once
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+    describe = plan.describe()
+    plan.destroy()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks = _peaks()
+    achieved = BYTES_PER_POINT * points / (ms_fwd * 1e-3) / 1e9
+    achieved_adj = BYTES_PER_POINT * points / (ms_adj * 1e-3) / 1e9
+    src_hash = _kernel_source_hash()
+    tr = NCU_TRAFFIC.get("fwd")
+    traffic = tr["bytes"] if tr and tr.get("hash") == src_hash else None
+    cpu = None if args.no_cpu_baseline else cpu_oracle_rate()
+    line = {
+        "metric": METRIC,
+        "value": world * points / (ms_fwd * 1e-3) / 1e9,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_fwd,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"bandwidth: N={N_POINTS} x {BATCH} FP32 planar forward, "
+                               "iid N(0,1) seed 1",
+                   "n": N_POINTS, "batch": BATCH, "per_gpu_points": points,
+                   "l2": "inputs larger than L2 (1 GiB moved per step), no flush",
+                   "schedule": describe, "parallelism": f"dp{world} (independent batches)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_source": f"{peaks['source']} (burst copy)",
+                     "frac_of_nominal_8tbs": achieved / 8000.0},
+        "adjoint": {"value": world * points / (ms_adj * 1e-3) / 1e9, "unit": UNIT,
+                    "ms_per_step": ms_adj, "achieved_gbs": achieved_adj,
+                    "frac": achieved_adj / peaks["hbm_gbs"]},
+        "copy_ceiling": {"gbs": BYTES_PER_POINT * points / (ms_copy * 1e-3) / 1e9,
+                         "what": "torch copy_ of both planes, same shape"},
+        "e2e": {"value": world * points / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * points * 4, "d2h_bytes_per_step": 2 * points * 4,
+                "api": "sdft_execute_host (pinned host buffers)"},
+        "cpu_baseline": cpu,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "kernel_source_hash": src_hash,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description="planar DFT benchmark (one JSON line)")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the CPU oracle timing (it is on by default)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * sdft.h -- C ABI of the planar split-complex DFT library (libsdft.so) for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The library computes the batched complex N-point discrete Fourier
+ * transform of A. Cariow, "Fast algorithms for complex-valued discrete
+ * Fourier transform with separate real and imaginary inputs/outputs"
+ * (arXiv 2504.07264), with real and imaginary parts kept in separate
+ * (planar) arrays from input to output:
+ *
+ *   forward  (Eq. (1), split form Eq. (3), block form Eqs. (4)-(5)):
+ *     y_k = sum_n x_n exp(-j 2 pi n k / N),
+ *     y^r = C x^r + S x^i,   y^i = C x^i - S x^r,
+ *     c_{k,n} = cos(2 pi k n / N),  s_{k,n} = sin(2 pi k n / N).
+ *   adjoint (the transpose of E_2N of Eq. (5), i.e. the conjugate transpose
+ *     of the DFT matrix, the unnormalised inverse DFT):
+ *     y^r = C x^r - S x^i,   y^i = S x^r + C x^i.
+ *
+ * Neither direction normalises (no 1/N): adjoint(forward(x)) = N x.
+ *
+ * Domain: N = 2^m with 1 <= m <= 16 (Section III takes N = 2^m, m >= 2; the
+ * same formulas hold for N = 2).  Other N: SDFT_ERR_UNSUPPORTED_N.
+ *
+ * Layout: each of xr, xi, yr, yi is a contiguous row-major float32 array of
+ * shape [batch][N] in device memory (transform b occupies elements
+ * b*N .. b*N+N-1).  Ragged plans use the transforms' rows concatenated in the
+ * order given, transform t starting at the exclusive prefix sum of the
+ * lengths before it.  The caller owns every buffer.  All four pointers must be
+ * 16-byte aligned.  Out-of-place, or fully in-place (yr == xr and yi == xi),
+ * are accepted; any other overlap among the four arrays is SDFT_ERR_ALIAS.
+ *
+ * Arithmetic: dtype SDFT_F32 computes in float32 with twiddle factors
+ * computed in float64 and rounded once to float32.  SDFT_F32_SPLIT_BF16 and
+ * SDFT_F32_SPLIT_FP16 run the dense radix blocks on tensor cores from hi/lo
+ * splits of the data and of the block (three products accumulated in
+ * float32); their input and output arrays are still float32.
+ *
+ * Streams and errors: every compute call is asynchronous on `stream` (a
+ * cudaStream_t passed as void*; NULL = the legacy default stream).  Each
+ * function returns an sdft status; argument errors are detected on the host
+ * before anything is enqueued.  A CUDA launch failure returns SDFT_ERR_CUDA.
+ * Calls must be made with the plan's device current (the device current at
+ * sdft_plan_create), otherwise SDFT_ERR_INVALID_ARG.
+ *
+ * Thread safety: a plan is immutable after creation; concurrent calls on one
+ * plan from several host threads or streams are safe, with two exceptions:
+ * plans of N >= 32768 own one scratch area that every call uses, so their
+ * calls must be ordered on one stream; and the *_host calls share the plan's
+ * staging buffers, so they must be serialised.
+ */
+#ifndef SDFT_H_
+#define SDFT_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SDFT_API __attribute__((visibility("default")))
+#else
+#define SDFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SDFT_OK                    0
+#define SDFT_ERR_INVALID_ARG       1  /* null pointer, batch < 1, bad direction, wrong device */
+#define SDFT_ERR_UNSUPPORTED_N     2  /* N not a power of two in [2, 65536] */
+#define SDFT_ERR_MISALIGNED        3  /* a data pointer not 16-byte aligned */
+#define SDFT_ERR_ALIAS             4  /* partial overlap of input and output arrays */
+#define SDFT_ERR_BAD_PLAN          5  /* NULL, destroyed or foreign plan handle */
+#define SDFT_ERR_CUDA              6  /* a CUDA runtime call failed */
+#define SDFT_ERR_ALLOC             7  /* host or device allocation failed */
+#define SDFT_ERR_TIMEOUT           8  /* a bounded device-side wait expired */
+#define SDFT_ERR_UNSUPPORTED_DTYPE 9  /* unknown dtype, or not offered for this N */
+
+/* ---- arithmetic paths (input/output are always float32 planar) ------- */
+#define SDFT_F32             0
+#define SDFT_F32_SPLIT_BF16  1
+#define SDFT_F32_SPLIT_FP16  2
+
+/* ---- directions -------------------------------------------------------- */
+#define SDFT_FORWARD 0   /* Eq. (1): E_2N of Eq. (5) */
+#define SDFT_ADJOINT 1   /* transpose of E_2N */
+
+typedef struct sdft_plan sdft_plan;
+
+/* Create a plan for `batch` transforms of length `n` (Section III: n = 2^m).
+ * Allocates the plan's device twiddle tables on the current device and
+ * synchronises that device once.  Returns NULL on error; sdft_last_error()
+ * then gives the status (SDFT_ERR_UNSUPPORTED_N, SDFT_ERR_INVALID_ARG,
+ * SDFT_ERR_UNSUPPORTED_DTYPE, SDFT_ERR_ALLOC, SDFT_ERR_CUDA). */
+SDFT_API sdft_plan* sdft_plan_create(int64_t n, int64_t batch, int dtype);
+
+/* Create a plan for a ragged batch: `count` transforms whose lengths
+ * lengths[0..count-1] (host array, read during the call only) are each a
+ * power of two in [4, 65536].  Rows are concatenated in the order given.
+ * Forward and adjoint calls on such a plan run as one persistent kernel
+ * launch that claims transforms, largest first, from a device work queue.
+ * Returns NULL on error (see sdft_last_error). */
+SDFT_API sdft_plan* sdft_plan_create_ragged(const int64_t* lengths, int64_t count, int dtype);
+
+/* Release a plan and its device memory.  NULL is ignored.  The caller must
+ * ensure no work using the plan is still in flight. */
+SDFT_API void sdft_plan_destroy(sdft_plan* plan);
+
+/* Forward transform (Eq. (1)/(3)) of every row: [yr; yi] = E_2N [xr; xi].
+ * xr, xi: input planes (device, float32, read only);
+ * yr, yi: output planes (device, float32, written);
+ * stream: cudaStream_t, or NULL.  Returns SDFT_OK or an error status. */
+SDFT_API int sdft_forward(const sdft_plan* plan, const float* xr, const float* xi,
+                 float* yr, float* yi, void* stream);
+
+/* Adjoint transform of every row: [yr; yi] = E_2N^T [xr; xi]
+ * (conjugate-transpose DFT, unnormalised).  Same arguments as sdft_forward. */
+SDFT_API int sdft_adjoint(const sdft_plan* plan, const float* xr, const float* xi,
+                 float* yr, float* yi, void* stream);
+
+/* Either direction (SDFT_FORWARD or SDFT_ADJOINT) through one entry point. */
+SDFT_API int sdft_execute(const sdft_plan* plan, int direction, const float* xr, const float* xi,
+                 float* yr, float* yi, void* stream);
+
+/* The same transform on HOST buffers: copies xr, xi to plan-owned device
+ * staging buffers, transforms, and copies the result back to yr, yi, in
+ * chunks pipelined over the plan's internal streams; returns after the
+ * result is in yr, yi.  Host buffers should be page-locked for full speed.
+ * The staging buffers (a few chunks, not the whole batch) are allocated by the
+ * first host call on a plan.  `stream`: work is ordered after prior work on it. */
+SDFT_API int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const float* xi,
+                      float* yr, float* yi, void* stream);
+
+/* Wait for `stream`, then read and clear the plan's device status word:
+ * SDFT_OK, or SDFT_ERR_TIMEOUT if a bounded device-side wait gave up. */
+SDFT_API int sdft_plan_sync_status(const sdft_plan* plan, void* stream);
+
+/* ---- introspection ----------------------------------------------------- */
+SDFT_API int64_t sdft_plan_n(const sdft_plan* plan);        /* N, or 0 for ragged plans */
+SDFT_API int64_t sdft_plan_batch(const sdft_plan* plan);    /* number of transforms */
+SDFT_API int64_t sdft_plan_points(const sdft_plan* plan);   /* total complex points per call */
+SDFT_API int     sdft_plan_dtype(const sdft_plan* plan);
+/* Kernel launches one sdft_forward/sdft_adjoint call makes. */
+SDFT_API int     sdft_plan_launches(const sdft_plan* plan, int direction);
+/* Human-readable schedule (radices, threads, I/O mode) into buf; returns the
+ * full length, like snprintf. */
+SDFT_API int     sdft_plan_describe(const sdft_plan* plan, char* buf, int64_t len);
+
+/* ---- errors ------------------------------------------------------------ */
+/* Status of the last failing call on this host thread (SDFT_OK if none). */
+SDFT_API int         sdft_last_error(void);
+/* Static English description of a status code. */
+SDFT_API const char* sdft_status_string(int status);
+/* Library version, "major.minor.patch". */
+SDFT_API const char* sdft_version(void);
+
+#ifdef __cplusplus
+}  /* extern "C" */
+#endif
+
+#endif  /* SDFT_H_ */

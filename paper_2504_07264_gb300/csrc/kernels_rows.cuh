@@ -1,0 +1,195 @@
+// kernels_rows.cuh -- batched planar FP32 DFT, one transform per thread group.
+//
+// Each transform (a contiguous row of N floats in each of xr, xi) is owned by
+// T = N / E threads of one CTA; a CTA holds G transforms.  Step 0 reads the
+// row straight from global memory with the thread <-> element map of the
+// step engine (consecutive threads read consecutive elements, so every warp
+// access is a full, aligned 128-byte line per plane); later steps exchange
+// through padded shared memory; the last step writes natural order straight
+// to global memory.  For N <= 32 one thread owns a whole row and moves it
+// with 16-byte vector loads and stores.
+//
+// The kernel is templated on direction: the forward kernel applies the
+// rotations W of Eq. (1); the adjoint kernel (E_2N^T) applies their
+// conjugates, i.e. the transposed 2x2 blocks omega^(i,q)^T.
+#pragma once
+
+#include "fft_core.cuh"
+#include "launch.h"
+
+namespace sdft {
+
+template <int LOGN, int LOGE, int LR0, int LR1, int LR2, int G_, int SBX_ = 0, int MINB_ = 1>
+struct RowCfg {
+    using S = Steps<LOGN, LOGE, LR0, LR1, LR2>;
+    static constexpr int G = G_;
+    static constexpr int THREADS = S::T * G;
+    static constexpr int MINB = MINB_;
+    static constexpr int PLANE = S::N + (S::N >> 5);
+    static constexpr int BUF = 2 * PLANE + SBX_;
+    static constexpr size_t SMEM = S::NS > 1 ? (size_t)G * BUF * sizeof(float) : 0;
+    static constexpr int64_t TW0 = 0;
+    static constexpr int64_t TW1 = S::NS > 1 ? S::tw_entries(0) : 0;
+    static constexpr int64_t TW_TOTAL = TW1 + (S::NS > 2 ? S::tw_entries(1) : 0);
+    static_assert(THREADS <= 1024, "CTA too large");
+    static_assert(S::T <= 32 || G == 1 || THREADS <= 1024, "");
+};
+
+template <class CFG, bool ADJ>
+__global__ void __launch_bounds__(CFG::THREADS, CFG::MINB)
+k_rows(const float* xr, const float* xi, float* yr, float* yi, long long batch,
+       const float2* __restrict__ tw, const W64 w) {
+    using S = typename CFG::S;
+    extern __shared__ float4 smem4[];
+    float* const smem = reinterpret_cast<float*>(smem4);
+    const int t = (int)threadIdx.x & (S::T - 1);
+    const int g = (int)threadIdx.x >> S::LOGT;
+    float* const s_re = smem + g * CFG::BUF;
+    float* const s_im = s_re + CFG::PLANE;
+
+    auto sync = [] {
+        if constexpr (S::T <= 32) __syncwarp();
+        else __syncthreads();
+    };
+    auto xw = [&](int L, float r, float i) {
+        const int p = pad32(L);
+        s_re[p] = r;
+        s_im[p] = i;
+    };
+    auto xrd = [&](int L, float& r, float& i) {
+        const int p = pad32(L);
+        r = s_re[p];
+        i = s_im[p];
+    };
+    auto twf = [&](int s, int d, int nl) -> float2 {
+        const int64_t off = (s == 0) ? CFG::TW0 : CFG::TW1;
+        const int q = (s == 0) ? (S::N >> S::lr(0)) : (S::N >> (S::lr(0) + S::lr(1)));
+        return __ldg(tw + off + (int64_t)d * q + nl);
+    };
+
+    const long long ntiles = (batch + CFG::G - 1) / CFG::G;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long b = tile * CFG::G + g;
+        const bool active = b < batch;
+        const long long row = (active ? b : 0) * (long long)S::N;
+        const float* gxr = xr + row;
+        const float* gxi = xi + row;
+        float* gyr = yr + row;
+        float* gyi = yi + row;
+
+        if constexpr (S::T == 1) {
+            // whole row per thread: vector loads into registers, then the
+            // step engine reads them by compile-time index.
+            constexpr int N = S::N;
+            float ar[N], ai[N];
+            if (active) {
+                if constexpr (N >= 4) {
+#pragma unroll
+                    for (int v = 0; v < N / 4; ++v) {
+                        const float4 a = reinterpret_cast<const float4*>(gxr)[v];
+                        const float4 c = reinterpret_cast<const float4*>(gxi)[v];
+                        ar[4 * v] = a.x; ar[4 * v + 1] = a.y; ar[4 * v + 2] = a.z; ar[4 * v + 3] = a.w;
+                        ai[4 * v] = c.x; ai[4 * v + 1] = c.y; ai[4 * v + 2] = c.z; ai[4 * v + 3] = c.w;
+                    }
+                } else {
+                    const float2 a = reinterpret_cast<const float2*>(gxr)[0];
+                    const float2 c = reinterpret_cast<const float2*>(gxi)[0];
+                    ar[0] = a.x; ar[1] = a.y;
+                    ai[0] = c.x; ai[1] = c.y;
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < N; ++v) { ar[v] = 0.f; ai[v] = 0.f; }
+            }
+            float orr[N], oi[N];
+            auto ld = [&](int L, float& r, float& i) { r = ar[L]; i = ai[L]; };
+            auto st = [&](int k, float r, float i) { orr[k] = r; oi[k] = i; };
+            run_steps<S, ADJ>(t, w, ld, xw, xrd, twf, st, sync);
+            if (active) {
+                if constexpr (N >= 4) {
+#pragma unroll
+                    for (int v = 0; v < N / 4; ++v) {
+                        reinterpret_cast<float4*>(gyr)[v] =
+                            make_float4(orr[4 * v], orr[4 * v + 1], orr[4 * v + 2], orr[4 * v + 3]);
+                        reinterpret_cast<float4*>(gyi)[v] =
+                            make_float4(oi[4 * v], oi[4 * v + 1], oi[4 * v + 2], oi[4 * v + 3]);
+                    }
+                } else {
+                    reinterpret_cast<float2*>(gyr)[0] = make_float2(orr[0], orr[1]);
+                    reinterpret_cast<float2*>(gyi)[0] = make_float2(oi[0], oi[1]);
+                }
+            }
+        } else {
+            auto ld = [&](int L, float& r, float& i) {
+                if (active) { r = gxr[L]; i = gxi[L]; }
+                else { r = 0.f; i = 0.f; }
+            };
+            auto st = [&](int k, float r, float i) {
+                if (active) { gyr[k] = r; gyi[k] = i; }
+            };
+            run_steps<S, ADJ>(t, w, ld, xw, xrd, twf, st, sync);
+            if constexpr (S::NS > 1) sync();  // last reads done before the next tile writes
+        }
+    }
+}
+
+template <class CFG>
+cudaError_t rows_prepare() {
+    cudaError_t e = cudaSuccess;
+    if (CFG::SMEM > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_rows<CFG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)CFG::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_rows<CFG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)CFG::SMEM);
+    }
+    return e;
+}
+
+template <class CFG>
+int rows_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rows<CFG, false>, CFG::THREADS,
+                                                      CFG::SMEM) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <class CFG>
+cudaError_t rows_launch(const LaunchArgs& a) {
+    if (a.adj)
+        return launch_kernel(k_rows<CFG, true>, a.grid, CFG::THREADS, CFG::SMEM, a.stream, a.xr,
+                             a.xi, a.yr, a.yi, a.batch, a.tw, a.w64);
+    return launch_kernel(k_rows<CFG, false>, a.grid, CFG::THREADS, CFG::SMEM, a.stream, a.xr,
+                         a.xi, a.yr, a.yi, a.batch, a.tw, a.w64);
+}
+
+template <class CFG>
+KernelInfo rows_info(const char* name) {
+    using S = typename CFG::S;
+    KernelInfo k = {};
+    k.name = name;
+    k.logn = S::LOGN;
+    k.threads = CFG::THREADS;
+    k.smem = CFG::SMEM;
+    k.transforms_per_cta = CFG::G;
+    k.ntables = 0;
+    if (S::NS > 1) {
+        const int64_t n = S::N;
+        k.tables[k.ntables++] = TableDesc{n, (int64_t)1 << S::lr(0), n >> S::lr(0), CFG::TW0};
+        if (S::NS > 2) {
+            const int64_t m1 = n >> S::lr(0);
+            k.tables[k.ntables++] =
+                TableDesc{m1, (int64_t)1 << S::lr(1), m1 >> S::lr(1), CFG::TW1};
+        }
+    }
+    k.tw_entries = CFG::TW_TOTAL;
+    k.scratch_per_cta = 0;
+    k.launches = 1;
+    k.prepare = rows_prepare<CFG>;
+    k.blocks_per_sm = rows_blocks_per_sm<CFG>;
+    k.launch = rows_launch<CFG>;
+    return k;
+}
+
+}  // namespace sdft

@@ -1,0 +1,374 @@
+// sdft_api.cu -- the C ABI declared in include/sdft.h: plan lifecycle,
+// argument validation, kernel dispatch and the host-buffer path.
+//
+// All validation happens on the host before anything is enqueued, so a bad
+// call never reaches the GPU.  Plans are tracked in a registry, so a NULL,
+// destroyed or foreign handle is rejected without being dereferenced.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+
+#include "../../include/sdft.h"
+#include "launch.h"
+
+namespace sdft {
+const KernelInfo* rows_kernel_small(int logn);
+const KernelInfo* rows_kernel_1024(int logn);
+const KernelInfo* rows_kernel_big(int logn);
+
+const KernelInfo* rows_kernel(int logn) {
+    if (logn >= 1 && logn <= 9) return rows_kernel_small(logn);
+    if (logn == 10) return rows_kernel_1024(logn);
+    if (logn >= 11 && logn <= 14) return rows_kernel_big(logn);
+    return nullptr;
+}
+}  // namespace sdft
+
+using namespace sdft;
+
+namespace {
+
+constexpr uint64_t kMagic = 0x53444654504c414eull;  // "SDFTPLAN"
+constexpr int kMaxLogN = 16;
+
+thread_local int g_last_error = SDFT_OK;
+
+int fail(int status) {
+    g_last_error = status;
+    return status;
+}
+
+struct HostStaging {
+    int64_t chunk = 0;                 // transforms per chunk
+    float* d_buf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [slot][plane]
+    cudaStream_t streams[2] = {nullptr, nullptr};
+    cudaEvent_t start = nullptr;
+    float2* d_scratch = nullptr;       // second scratch set for the second slot
+};
+
+}  // namespace
+
+struct sdft_plan {
+    uint64_t magic;
+    int device;
+    int dtype;
+    int64_t n;            // 0 for ragged plans
+    int64_t batch;
+    int64_t points;
+    const KernelInfo* kern;
+    int grid;
+    float2* d_tw;
+    float2* d_scratch;
+    int* d_status;
+    W64 w64;
+    HostStaging host;
+};
+
+namespace {
+
+std::mutex g_registry_mu;
+std::set<const sdft_plan*> g_registry;
+
+bool plan_alive(const sdft_plan* p) {
+    if (p == nullptr) return false;
+    std::lock_guard<std::mutex> lk(g_registry_mu);
+    return g_registry.count(p) != 0 && p->magic == kMagic;
+}
+
+int log2_exact(int64_t n) {
+    if (n < 1) return -1;
+    int m = 0;
+    while (((int64_t)1 << m) < n) ++m;
+    return (((int64_t)1 << m) == n) ? m : -1;
+}
+
+void free_plan_memory(sdft_plan* p) {
+    if (p->d_tw) cudaFree(p->d_tw);
+    if (p->d_scratch) cudaFree(p->d_scratch);
+    if (p->d_status) cudaFree(p->d_status);
+    for (int s = 0; s < 2; ++s) {
+        for (int pl = 0; pl < 2; ++pl)
+            if (p->host.d_buf[s][pl]) cudaFree(p->host.d_buf[s][pl]);
+        if (p->host.streams[s]) cudaStreamDestroy(p->host.streams[s]);
+    }
+    if (p->host.start) cudaEventDestroy(p->host.start);
+    if (p->host.d_scratch) cudaFree(p->host.d_scratch);
+}
+
+bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+int check_buffers(const sdft_plan* p, const float* xr, const float* xi, const float* yr,
+                  const float* yi) {
+    if (!xr || !xi || !yr || !yi) return SDFT_ERR_INVALID_ARG;
+    const uintptr_t a[4] = {(uintptr_t)xr, (uintptr_t)xi, (uintptr_t)yr, (uintptr_t)yi};
+    for (uintptr_t v : a)
+        if (v % 16 != 0) return SDFT_ERR_MISALIGNED;
+    const size_t bytes = (size_t)p->points * sizeof(float);
+    // outputs must not overlap each other
+    if (ranges_overlap(yr, yi, bytes)) return SDFT_ERR_ALIAS;
+    // an output may coincide exactly with its own input (in place) and may
+    // not otherwise overlap any input
+    const bool in_place = (yr == xr) && (yi == xi);
+    if (in_place) {
+        if (ranges_overlap(yr, xi, bytes) || ranges_overlap(yi, xr, bytes)) return SDFT_ERR_ALIAS;
+    } else {
+        if (ranges_overlap(yr, xr, bytes) || ranges_overlap(yr, xi, bytes) ||
+            ranges_overlap(yi, xr, bytes) || ranges_overlap(yi, xi, bytes))
+            return SDFT_ERR_ALIAS;
+    }
+    return SDFT_OK;
+}
+
+int check_device(const sdft_plan* p) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SDFT_ERR_CUDA;
+    return dev == p->device ? SDFT_OK : SDFT_ERR_INVALID_ARG;
+}
+
+int launch(const sdft_plan* p, int direction, const float* xr, const float* xi, float* yr,
+           float* yi, cudaStream_t stream, long long batch, float2* scratch) {
+    LaunchArgs a;
+    a.xr = xr;
+    a.xi = xi;
+    a.yr = yr;
+    a.yi = yi;
+    a.batch = batch;
+    a.tw = p->d_tw;
+    a.w64 = p->w64;
+    a.scratch = scratch;
+    a.status = p->d_status;
+    a.grid = p->grid;
+    a.stream = stream;
+    a.adj = (direction == SDFT_ADJOINT);
+    const long long tiles = (batch + p->kern->transforms_per_cta - 1) / p->kern->transforms_per_cta;
+    if (scratch == nullptr && tiles < a.grid) a.grid = (int)std::max<long long>(tiles, 1);
+    return p->kern->launch(a) == cudaSuccess ? SDFT_OK : SDFT_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sdft_version(void) { return "0.1.0"; }
+
+int sdft_last_error(void) { return g_last_error; }
+
+const char* sdft_status_string(int status) {
+    switch (status) {
+        case SDFT_OK: return "ok";
+        case SDFT_ERR_INVALID_ARG: return "invalid argument";
+        case SDFT_ERR_UNSUPPORTED_N: return "unsupported transform length (need a power of two in [2, 65536])";
+        case SDFT_ERR_MISALIGNED: return "data pointer not 16-byte aligned";
+        case SDFT_ERR_ALIAS: return "input and output arrays partially overlap";
+        case SDFT_ERR_BAD_PLAN: return "invalid or destroyed plan";
+        case SDFT_ERR_CUDA: return "CUDA runtime error";
+        case SDFT_ERR_ALLOC: return "allocation failed";
+        case SDFT_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SDFT_ERR_UNSUPPORTED_DTYPE: return "unsupported dtype";
+        default: return "unknown status";
+    }
+}
+
+sdft_plan* sdft_plan_create(int64_t n, int64_t batch, int dtype) {
+    const int logn = log2_exact(n);
+    if (logn < 1 || logn > kMaxLogN) { fail(SDFT_ERR_UNSUPPORTED_N); return nullptr; }
+    if (batch < 1) { fail(SDFT_ERR_INVALID_ARG); return nullptr; }
+    if (dtype != SDFT_F32) { fail(SDFT_ERR_UNSUPPORTED_DTYPE); return nullptr; }
+    if (batch > ((int64_t)1 << 40) / n) { fail(SDFT_ERR_INVALID_ARG); return nullptr; }
+
+    const KernelInfo* k = logn <= 14 ? rows_kernel(logn) : large_kernel(logn);
+    if (!k) { fail(SDFT_ERR_UNSUPPORTED_N); return nullptr; }
+
+    sdft_plan* p = new (std::nothrow) sdft_plan();
+    if (!p) { fail(SDFT_ERR_ALLOC); return nullptr; }
+    p->magic = 0;
+    p->dtype = dtype;
+    p->n = n;
+    p->batch = batch;
+    p->points = n * batch;
+    p->kern = k;
+    int status = SDFT_OK;
+    cudaStream_t st = nullptr;
+    do {
+        if (cudaGetDevice(&p->device) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+            status = SDFT_ERR_CUDA; break;
+        }
+        if (k->prepare() != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        const int bps = std::max(1, k->blocks_per_sm());
+        p->grid = bps * sms;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            status = SDFT_ERR_CUDA; break;
+        }
+        const int64_t tw_entries = std::max<int64_t>(k->tw_entries, 64);
+        if (cudaMalloc(&p->d_tw, tw_entries * sizeof(float2)) != cudaSuccess) {
+            status = SDFT_ERR_ALLOC; break;
+        }
+        if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) { status = SDFT_ERR_ALLOC; break; }
+        if (cudaMemsetAsync(p->d_status, 0, sizeof(int), st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        if (k->scratch_per_cta > 0) {
+            const size_t bytes = (size_t)p->grid * (size_t)k->scratch_per_cta * sizeof(float2);
+            if (cudaMalloc(&p->d_scratch, bytes) != cudaSuccess) { status = SDFT_ERR_ALLOC; break; }
+        }
+        // the register constants first (uses the table memory as scratch)
+        if (make_w64(&p->w64, p->d_tw, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        if (make_tables(p->d_tw, k->tables, k->ntables, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        if (cudaStreamSynchronize(st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+    } while (0);
+    if (st) cudaStreamDestroy(st);
+    if (status != SDFT_OK) {
+        free_plan_memory(p);
+        delete p;
+        fail(status);
+        return nullptr;
+    }
+    p->magic = kMagic;
+    {
+        std::lock_guard<std::mutex> lk(g_registry_mu);
+        g_registry.insert(p);
+    }
+    return p;
+}
+
+sdft_plan* sdft_plan_create_ragged(const int64_t* lengths, int64_t count, int dtype) {
+    (void)lengths;
+    (void)count;
+    (void)dtype;
+    fail(SDFT_ERR_UNSUPPORTED_N);
+    return nullptr;
+}
+
+void sdft_plan_destroy(sdft_plan* plan) {
+    if (plan == nullptr) return;
+    {
+        std::lock_guard<std::mutex> lk(g_registry_mu);
+        if (g_registry.erase(plan) == 0) return;  // not ours, or already destroyed
+    }
+    plan->magic = 0;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != plan->device) cudaSetDevice(plan->device);
+    free_plan_memory(plan);
+    if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
+    delete plan;
+}
+
+int sdft_execute(const sdft_plan* plan, int direction, const float* xr, const float* xi,
+                 float* yr, float* yi, void* stream) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    if (direction != SDFT_FORWARD && direction != SDFT_ADJOINT) return fail(SDFT_ERR_INVALID_ARG);
+    int s = check_buffers(plan, xr, xi, yr, yi);
+    if (s != SDFT_OK) return fail(s);
+    s = check_device(plan);
+    if (s != SDFT_OK) return fail(s);
+    s = launch(plan, direction, xr, xi, yr, yi, (cudaStream_t)stream, plan->batch, plan->d_scratch);
+    if (s != SDFT_OK) return fail(s);
+    return SDFT_OK;
+}
+
+int sdft_forward(const sdft_plan* plan, const float* xr, const float* xi, float* yr, float* yi,
+                 void* stream) {
+    return sdft_execute(plan, SDFT_FORWARD, xr, xi, yr, yi, stream);
+}
+
+int sdft_adjoint(const sdft_plan* plan, const float* xr, const float* xi, float* yr, float* yi,
+                 void* stream) {
+    return sdft_execute(plan, SDFT_ADJOINT, xr, xi, yr, yi, stream);
+}
+
+int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const float* xi, float* yr,
+                      float* yi, void* stream) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    if (direction != SDFT_FORWARD && direction != SDFT_ADJOINT) return fail(SDFT_ERR_INVALID_ARG);
+    if (!xr || !xi || !yr || !yi) return fail(SDFT_ERR_INVALID_ARG);
+    int s = check_device(plan);
+    if (s != SDFT_OK) return fail(s);
+    HostStaging& h = plan->host;
+    const int64_t n = plan->n;
+    if (h.chunk == 0) {
+        // ~32 MiB per plane per slot, whole transforms, at least one
+        int64_t chunk = std::max<int64_t>(1, ((int64_t)32 << 20) / (n * (int64_t)sizeof(float)));
+        chunk = std::min<int64_t>(chunk, plan->batch);
+        for (int sl = 0; sl < 2; ++sl) {
+            for (int pl = 0; pl < 2; ++pl)
+                if (cudaMalloc(&h.d_buf[sl][pl], (size_t)chunk * n * sizeof(float)) != cudaSuccess)
+                    return fail(SDFT_ERR_ALLOC);
+            if (cudaStreamCreateWithFlags(&h.streams[sl], cudaStreamNonBlocking) != cudaSuccess)
+                return fail(SDFT_ERR_CUDA);
+        }
+        if (cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming) != cudaSuccess)
+            return fail(SDFT_ERR_CUDA);
+        if (plan->kern->scratch_per_cta > 0) {
+            const size_t sb = (size_t)plan->grid * (size_t)plan->kern->scratch_per_cta * sizeof(float2);
+            if (cudaMalloc(&h.d_scratch, sb) != cudaSuccess) return fail(SDFT_ERR_ALLOC);
+        }
+        h.chunk = chunk;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    if (cudaEventRecord(h.start, user) != cudaSuccess) return fail(SDFT_ERR_CUDA);
+    for (int sl = 0; sl < 2; ++sl)
+        if (cudaStreamWaitEvent(h.streams[sl], h.start, 0) != cudaSuccess) return fail(SDFT_ERR_CUDA);
+    const int64_t nchunks = (plan->batch + h.chunk - 1) / h.chunk;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int sl = (int)(c & 1);
+        cudaStream_t st = h.streams[sl];
+        const int64_t b0 = c * h.chunk;
+        const int64_t nb = std::min<int64_t>(h.chunk, plan->batch - b0);
+        const size_t off = (size_t)b0 * n, bytes = (size_t)nb * n * sizeof(float);
+        float* dr = h.d_buf[sl][0];
+        float* di = h.d_buf[sl][1];
+        if (cudaMemcpyAsync(dr, xr + off, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(di, xi + off, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return fail(SDFT_ERR_CUDA);
+        s = launch(plan, direction, dr, di, dr, di, st, nb, sl == 0 ? plan->d_scratch : h.d_scratch);
+        if (s != SDFT_OK) return fail(s);
+        if (cudaMemcpyAsync(yr + off, dr, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(yi + off, di, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return fail(SDFT_ERR_CUDA);
+    }
+    for (int sl = 0; sl < 2; ++sl)
+        if (cudaStreamSynchronize(h.streams[sl]) != cudaSuccess) return fail(SDFT_ERR_CUDA);
+    return SDFT_OK;
+}
+
+int sdft_plan_sync_status(const sdft_plan* plan, void* stream) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    int s = check_device(plan);
+    if (s != SDFT_OK) return fail(s);
+    int h = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(plan->d_status, 0, sizeof(int), st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(SDFT_ERR_CUDA);
+    return h == 0 ? SDFT_OK : fail(h);
+}
+
+int64_t sdft_plan_n(const sdft_plan* plan) { return plan_alive(plan) ? plan->n : 0; }
+int64_t sdft_plan_batch(const sdft_plan* plan) { return plan_alive(plan) ? plan->batch : 0; }
+int64_t sdft_plan_points(const sdft_plan* plan) { return plan_alive(plan) ? plan->points : 0; }
+int sdft_plan_dtype(const sdft_plan* plan) { return plan_alive(plan) ? plan->dtype : -1; }
+
+int sdft_plan_launches(const sdft_plan* plan, int direction) {
+    (void)direction;
+    return plan_alive(plan) ? plan->kern->launches : 0;
+}
+
+int sdft_plan_describe(const sdft_plan* plan, char* buf, int64_t len) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN), -1;
+    return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
+                         "%s; %d threads/CTA, %zu B smem, grid %d, %d transform(s)/CTA tile",
+                         plan->kern->name, plan->kern->threads, plan->kern->smem, plan->grid,
+                         plan->kern->transforms_per_cta);
+}
+
+}  // extern "C"

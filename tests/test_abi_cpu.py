@@ -1,0 +1,88 @@
+"""The C ABI library builds, loads and exports every declared symbol; host-side
+argument checks work without a GPU (no compute call is made here)."""
+import ctypes
+import re
+import subprocess
+
+import pytest
+
+from paper_2504_07264_gb300 import build as B
+from paper_2504_07264_gb300 import sdft as S
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    B.build()
+
+
+def test_exports_every_header_symbol():
+    names = S.header_symbols()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(S.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+    # and nothing else leaks out of the library as a dynamic symbol
+    out = subprocess.run(["nm", "-D", "--defined-only", S.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    assert set(names) <= exported
+    assert all(not n.startswith("_ZN4sdft") for n in exported)
+
+
+def test_binding_covers_header():
+    assert set(S.header_symbols()) == set(S._SIGS)
+
+
+def test_header_constants_match_binding():
+    with open(S.HEADER) as f:
+        text = f.read()
+    defs = dict(re.findall(r"#define\s+(SDFT_\w+)\s+(-?\d+)", text))
+    assert defs, "no constants parsed"
+    for name, val in defs.items():
+        assert getattr(S, name) == int(val), name
+
+
+def test_version_and_status_strings():
+    assert re.fullmatch(r"\d+\.\d+\.\d+", S.sdft_version())
+    for code in range(10):
+        assert S.sdft_status_string(code)
+    assert S.sdft_status_string(0) == "ok"
+    assert "unknown" in S.sdft_status_string(999)
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 6, 1000, 1 << 17, -4])
+def test_unsupported_length_rejected_before_cuda(n):
+    assert S.sdft_plan_create(n, 4, S.SDFT_F32) == 0
+    assert S.sdft_last_error() == S.SDFT_ERR_UNSUPPORTED_N
+
+
+@pytest.mark.parametrize("batch", [0, -1])
+def test_bad_batch_rejected(batch):
+    assert S.sdft_plan_create(1024, batch, S.SDFT_F32) == 0
+    assert S.sdft_last_error() == S.SDFT_ERR_INVALID_ARG
+
+
+def test_bad_dtype_rejected():
+    assert S.sdft_plan_create(1024, 4, 7) == 0
+    assert S.sdft_last_error() == S.SDFT_ERR_UNSUPPORTED_DTYPE
+
+
+@pytest.mark.parametrize("handle", [0, 12345678, 0xDEADBEEF0])
+def test_bad_plan_handles(handle):
+    assert S.sdft_forward(handle, 16, 16, 16, 16, 0) == S.SDFT_ERR_BAD_PLAN
+    assert S.sdft_adjoint(handle, 16, 16, 16, 16, 0) == S.SDFT_ERR_BAD_PLAN
+    assert S.sdft_execute(handle, 0, 16, 16, 16, 16, 0) == S.SDFT_ERR_BAD_PLAN
+    assert S.sdft_execute_host(handle, 0, 16, 16, 16, 16, 0) == S.SDFT_ERR_BAD_PLAN
+    assert S.sdft_plan_sync_status(handle, 0) == S.SDFT_ERR_BAD_PLAN
+    assert S.sdft_last_error() == S.SDFT_ERR_BAD_PLAN
+    assert S.sdft_plan_n(handle) == 0 and S.sdft_plan_launches(handle, 0) == 0
+    S.sdft_plan_destroy(handle)  # foreign handles are ignored, not freed
+
+
+def test_ragged_rejects_bad_lengths_before_cuda():
+    import numpy as np
+    for lengths in ([8, 12], [8, 2], [], [1 << 17]):
+        arr = np.asarray(lengths, dtype=np.int64)
+        h = S.sdft_plan_create_ragged(arr.ctypes.data if arr.size else 0, arr.size, S.SDFT_F32)
+        assert h == 0
+        assert S.sdft_last_error() in (S.SDFT_ERR_UNSUPPORTED_N, S.SDFT_ERR_INVALID_ARG)
