@@ -247,13 +247,14 @@ def run_ours(args) -> None:
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    xr_h, xi_h = workloads.bandwidth()
-    points = N_POINTS * BATCH
+    batch = args.batch
+    xr_h, xi_h = workloads.bandwidth(batch)
+    points = N_POINTS * batch
     xr = torch.from_numpy(xr_h).cuda()
     xi = torch.from_numpy(xi_h).cuda()
     yr = torch.empty_like(xr)
     yi = torch.empty_like(xi)
-    plan = Plan(N_POINTS, BATCH)
+    plan = Plan(N_POINTS, batch)
     launches_per_step = plan.launches(SDFT_FORWARD)
 
     fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
@@ -287,22 +288,24 @@ def run_ours(args) -> None:
         ms_fwd, ms_adj = t.tolist()
 
     # end to end through the C ABI on pinned host buffers
-    hxr = torch.from_numpy(xr_h).pin_memory()
-    hxi = torch.from_numpy(xi_h).pin_memory()
-    hyr = torch.empty_like(hxr).pin_memory()
-    hyi = torch.empty_like(hxi).pin_memory()
-    e2e_steps = max(1, min(args.steps, 10))
-    plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)   # allocates staging once
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)
-    barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
+    e2e_s = None
+    if not args.no_e2e:
+        hxr = torch.from_numpy(xr_h).pin_memory()
+        hxi = torch.from_numpy(xi_h).pin_memory()
+        hyr = torch.empty_like(hxr).pin_memory()
+        hyi = torch.empty_like(hxi).pin_memory()
+        e2e_steps = max(1, min(args.steps, 10))
+        plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)   # allocates staging once
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = t.item()
     describe = plan.describe()
     plan.destroy()
 
@@ -330,9 +333,9 @@ def run_ours(args) -> None:
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"bandwidth: N={N_POINTS} x {BATCH} FP32 planar forward, "
+        "config": {"workload": f"bandwidth: N={N_POINTS} x {batch} FP32 planar forward, "
                                "iid N(0,1) seed 1",
-                   "n": N_POINTS, "batch": BATCH, "per_gpu_points": points,
+                   "n": N_POINTS, "batch": batch, "per_gpu_points": points,
                    "l2": "inputs larger than L2 (1 GiB moved per step), no flush",
                    "schedule": describe, "parallelism": f"dp{world} (independent batches)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
@@ -344,9 +347,10 @@ def run_ours(args) -> None:
                     "frac": achieved_adj / peaks["hbm_gbs"]},
         "copy_ceiling": {"gbs": BYTES_PER_POINT * points / (ms_copy * 1e-3) / 1e9,
                          "what": "torch copy_ of both planes, same shape"},
-        "e2e": {"value": world * points / e2e_s / 1e9, "unit": UNIT,
-                "h2d_bytes_per_step": 2 * points * 4, "d2h_bytes_per_step": 2 * points * 4,
-                "api": "sdft_execute_host (pinned host buffers)"},
+        "e2e": None if e2e_s is None else {
+            "value": world * points / e2e_s / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": 2 * points * 4, "d2h_bytes_per_step": 2 * points * 4,
+            "api": "sdft_execute_host (pinned host buffers)"},
         "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -365,6 +369,11 @@ def main(argv=None) -> int:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the CPU oracle timing (it is on by default)")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the host-buffer end-to-end leg (it is on by default)")
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="transforms per step (default: the full 65536; smaller only "
+                         "for profiling captures, never for a reported number)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
