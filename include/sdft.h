@@ -134,6 +134,23 @@ SDFT_API int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, 
  * SDFT_OK, or SDFT_ERR_TIMEOUT if a bounded device-side wait gave up. */
 SDFT_API int sdft_plan_sync_status(const sdft_plan* plan, void* stream);
 
+/* ---- allocation-free long transforms ---------------------------------- */
+/* The paper has no counterpart to this entry point.
+ * For callers that cannot allocate device memory (their memory is owned by
+ * another allocator or capped, or they must avoid the synchronisation that
+ * cudaMalloc/cudaFree can cause): transform `batch` rows of length n = 32768
+ * or 65536 -- the lengths whose kernel needs global scratch -- without a plan
+ * and without any allocation.  Scratch and twiddle tables live in file-scope
+ * device arrays of libsdft.so that every GPU loading the library holds until
+ * the process exits; the scratch is 8 MiB (16 slots of 65536 or 32 of 32768
+ * complex values).  Arguments as sdft_execute; n other than 32768 or 65536:
+ * SDFT_ERR_UNSUPPORTED_N.  The first call on a device sets up that device
+ * (resolves the arrays, fills the tables, synchronises the device): make it
+ * before any stream capture.  All calls share the arrays, so calls that
+ * overlap on the GPU race; order them on one stream. */
+SDFT_API int sdft_execute_noalloc(int64_t n, int64_t batch, int direction, const float* xr,
+                                  const float* xi, float* yr, float* yi, void* stream);
+
 /* ---- introspection ----------------------------------------------------- */
 SDFT_API int64_t sdft_plan_n(const sdft_plan* plan);        /* N, or 0 for ragged plans */
 SDFT_API int64_t sdft_plan_batch(const sdft_plan* plan);    /* number of transforms */

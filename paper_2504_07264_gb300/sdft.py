@@ -49,6 +49,7 @@ _SIGS = {
     "sdft_execute": ([_P, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
     "sdft_execute_host": ([_P, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
     "sdft_plan_sync_status": ([_P, _P], ctypes.c_int),
+    "sdft_execute_noalloc": ([_I64, _I64, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
     "sdft_plan_n": ([_P], _I64),
     "sdft_plan_batch": ([_P], _I64),
     "sdft_plan_points": ([_P], _I64),
@@ -123,6 +124,10 @@ def sdft_execute(plan, direction, xr, xi, yr, yi, stream) -> int:
 
 def sdft_execute_host(plan, direction, xr, xi, yr, yi, stream) -> int:
     return lib().sdft_execute_host(plan, direction, xr, xi, yr, yi, stream)
+
+
+def sdft_execute_noalloc(n, batch, direction, xr, xi, yr, yi, stream) -> int:
+    return lib().sdft_execute_noalloc(n, batch, direction, xr, xi, yr, yi, stream)
 
 
 def sdft_plan_sync_status(plan, stream) -> int:
