@@ -361,6 +361,147 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def _measure_uniform(n: int, batch: int, xr_h, xi_h, steps: int, warmup: int, stream) -> dict:
+    """Forward and adjoint kernel times of one uniform plan (one GPU)."""
+    import torch
+
+    from paper_2504_07264_gb300 import SDFT_ADJOINT, SDFT_FORWARD, Plan
+    xr = torch.from_numpy(xr_h).cuda()
+    xi = torch.from_numpy(xi_h).cuda()
+    yr = torch.empty_like(xr)
+    yi = torch.empty_like(xi)
+    points = n * batch
+    peak = _peaks()["hbm_gbs"]
+    with Plan(n, batch) as plan:
+        fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
+        adj = lambda: plan.execute(SDFT_ADJOINT, xr, xi, yr, yi, stream)  # noqa: E731
+        for _ in range(warmup):
+            fwd()
+            adj()
+        torch.cuda.synchronize()
+        ms_f = _time_steps(fwd, steps, stream)
+        ms_a = _time_steps(adj, steps, stream)
+        out = {"n": n, "batch": batch, "schedule": plan.describe(),
+               "launches_per_call": plan.launches(SDFT_FORWARD)}
+    for name, ms in (("forward", ms_f), ("adjoint", ms_a)):
+        gbs = BYTES_PER_POINT * points / (ms * 1e-3) / 1e9
+        out[name] = {"gpts": points / (ms * 1e-3) / 1e9, "ms": ms, "gbs": gbs, "frac": gbs / peak}
+    return out
+
+
+def run_workload(args) -> None:
+    """Single-GPU measurements of the other configurations (one JSON line)."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2504_07264_gb300 import build as cuda_build
+    cuda_build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    peak = _peaks()["hbm_gbs"]
+    line = {"workload": args.workload, "unit": UNIT, "peak_gbs": peak, "steps": args.steps,
+            "warmup": args.warmup}
+    if args.workload == "autograd":
+        from paper_2504_07264_gb300 import split_dft
+        cfg = workloads.AUTOGRAD
+        n, batch = cfg["n"], cfg["batch"]
+        xr_h, xi_h = workloads.normal_planes(n, batch, cfg["seed"])
+        line.update(_measure_uniform(n, batch, xr_h, xi_h, args.steps, args.warmup, stream))
+        wr_h, wi_h = workloads.loss_weights(n, batch, cfg["weight_seed"])
+        xr = torch.from_numpy(xr_h).cuda().requires_grad_(True)
+        xi = torch.from_numpy(xi_h).cuda().requires_grad_(True)
+        wr, wi = torch.from_numpy(wr_h).cuda(), torch.from_numpy(wi_h).cuda()
+
+        def step():
+            xr.grad = None
+            xi.grad = None
+            yr, yi = split_dft(xr, xi)
+            (wr * yr ** 2 + wi * yi ** 2).sum().backward()
+        for _ in range(args.warmup):
+            step()
+        ms = _time_steps(step, max(5, args.steps // 10), stream)
+        line["autograd_step"] = {"ms": ms, "gpts": n * batch / (ms * 1e-3) / 1e9,
+                                 "what": "split_dft forward + weighted-square loss + backward "
+                                         "(adjoint kernel), torch elementwise ops included"}
+        line["metric"] = "planar DFT Gpts/s, N=4096 B=16384, fwd + adj kernels and autograd step"
+        line["value"] = line["forward"]["gpts"]
+    elif args.workload == "precision":
+        cfg = workloads.PRECISION
+        n, batch = cfg["n"], cfg["batch"]
+        xr_h, xi_h = workloads.precision()
+        line.update(_measure_uniform(n, batch, xr_h, xi_h, args.steps, args.warmup, stream))
+        line["metric"] = "planar DFT Gpts/s, N=256 B=262144 (FP32 path)"
+        line["value"] = line["forward"]["gpts"]
+    elif args.workload == "ragged":
+        from paper_2504_07264_gb300 import SDFT_ADJOINT, SDFT_FORWARD, Plan
+        lengths, off, xr_h, xi_h = workloads.ragged_planes()
+        points = int(off[-1])
+        xr = torch.from_numpy(xr_h).cuda()
+        xi = torch.from_numpy(xi_h).cuda()
+        yr = torch.empty_like(xr)
+        yi = torch.empty_like(xi)
+        with Plan(lengths=lengths) as plan:
+            fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
+            adj = lambda: plan.execute(SDFT_ADJOINT, xr, xi, yr, yi, stream)  # noqa: E731
+            for _ in range(args.warmup):
+                fwd()
+                adj()
+            torch.cuda.synchronize()
+            ms_f = _time_steps(fwd, args.steps, stream)
+            ms_a = _time_steps(adj, args.steps, stream)
+            line["schedule"] = plan.describe()
+            line["launches_per_call"] = plan.launches(SDFT_FORWARD)
+        for name, ms in (("forward", ms_f), ("adjoint", ms_a)):
+            gbs = BYTES_PER_POINT * points / (ms * 1e-3) / 1e9
+            line[name] = {"gpts": points / (ms * 1e-3) / 1e9, "ms": ms, "gbs": gbs,
+                          "frac": gbs / peak}
+        # the same transforms as one uniform plan per length (one launch each),
+        # on per-length contiguous copies of the data
+        plans, bufs = [], []
+        for logn in range(2, 17):
+            sel = np.nonzero(lengths == (1 << logn))[0]
+            if sel.size == 0:
+                continue
+            rows_r = np.concatenate([xr_h[off[t]:off[t + 1]] for t in sel])
+            rows_i = np.concatenate([xi_h[off[t]:off[t + 1]] for t in sel])
+            a = torch.from_numpy(rows_r).cuda()
+            b = torch.from_numpy(rows_i).cuda()
+            bufs.append((a, b, torch.empty_like(a), torch.empty_like(b)))
+            plans.append(Plan(1 << logn, int(sel.size)))
+
+        def per_length():
+            for pl, (a, b, c, d) in zip(plans, bufs):
+                pl.execute(SDFT_FORWARD, a, b, c, d, stream)
+        for _ in range(args.warmup):
+            per_length()
+        ms_u = _time_steps(per_length, args.steps, stream)
+        for pl in plans:
+            pl.destroy()
+        gbs = BYTES_PER_POINT * points / (ms_u * 1e-3) / 1e9
+        line["per_length_uniform_kernels"] = {
+            "gpts": points / (ms_u * 1e-3) / 1e9, "ms": ms_u, "gbs": gbs, "frac": gbs / peak,
+            "launches": len(plans), "what": "one uniform FP32 plan per length, data pre-sorted"}
+        line["points"] = points
+        line["metric"] = ("planar DFT Gpts/s, ragged batch of 10000 transforms, lengths 2^U{3..16} "
+                          "(seed 4), one persistent launch in a CUDA graph")
+        line["value"] = line["forward"]["gpts"]
+    elif args.workload == "sizes":
+        rows = []
+        for logn in range(1, 17):
+            n = 1 << logn
+            batch = (1 << 26) // n
+            xr_h, xi_h = workloads.normal_planes(n, batch, seed=1)
+            r = _measure_uniform(n, batch, xr_h, xi_h, max(20, args.steps // 10), args.warmup,
+                                 stream)
+            rows.append({k: r[k] for k in ("n", "batch", "forward", "adjoint", "schedule")})
+            del xr_h, xi_h
+        line["sizes"] = rows
+        line["metric"] = "planar DFT Gpts/s per N, 2^26 points per step"
+        line["value"] = None
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description="planar DFT benchmark (one JSON line)")
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,6 +512,10 @@ def main(argv=None) -> int:
                     help="skip the CPU oracle timing (it is on by default)")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the host-buffer end-to-end leg (it is on by default)")
+    ap.add_argument("--workload", choices=("bandwidth", "autograd", "precision", "ragged", "sizes"),
+                    default="bandwidth",
+                    help="bandwidth (default) is the headline line; the others print one "
+                         "single-GPU line of their own")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="transforms per step (default: the full 65536; smaller only "
                          "for profiling captures, never for a reported number)")
@@ -379,6 +524,8 @@ def main(argv=None) -> int:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "bandwidth":
+        run_workload(args)
     else:
         run_ours(args)
     return 0

@@ -35,18 +35,15 @@ struct RowCfg {
     static_assert(S::T <= 32 || G == 1 || THREADS <= 1024, "");
 };
 
+// One tile of CFG: group g (the caller's `t`, `s_re`, `s_im` belong to it)
+// transforms the row at gxr/gxi into gyr/gyi when `active`.  Every thread of
+// the CTA must call this (inactive groups still take part in the barriers).
 template <class CFG, bool ADJ>
-__global__ void __launch_bounds__(CFG::THREADS, CFG::MINB)
-k_rows(const float* xr, const float* xi, float* yr, float* yi, long long batch,
-       const float2* __restrict__ tw, const W64 w) {
+__device__ __forceinline__ void rows_tile(const float* gxr, const float* gxi, float* gyr,
+                                          float* gyi, const bool active, const int t,
+                                          float* const s_re, float* const s_im,
+                                          const float2* __restrict__ tw, const W64& w) {
     using S = typename CFG::S;
-    extern __shared__ float4 smem4[];
-    float* const smem = reinterpret_cast<float*>(smem4);
-    const int t = (int)threadIdx.x & (S::T - 1);
-    const int g = (int)threadIdx.x >> S::LOGT;
-    float* const s_re = smem + g * CFG::BUF;
-    float* const s_im = s_re + CFG::PLANE;
-
     auto sync = [] {
         if constexpr (S::T <= 32) __syncwarp();
         else __syncthreads();
@@ -66,70 +63,78 @@ k_rows(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         const int q = (s == 0) ? (S::N >> S::lr(0)) : (S::N >> (S::lr(0) + S::lr(1)));
         return __ldg(tw + off + (int64_t)d * q + nl);
     };
+    if constexpr (S::T == 1) {
+        // whole row per thread: vector loads into registers, then the step
+        // engine reads them by compile-time index.
+        constexpr int N = S::N;
+        float ar[N], ai[N];
+        if (active) {
+            if constexpr (N >= 4) {
+#pragma unroll
+                for (int v = 0; v < N / 4; ++v) {
+                    const float4 a = reinterpret_cast<const float4*>(gxr)[v];
+                    const float4 c = reinterpret_cast<const float4*>(gxi)[v];
+                    ar[4 * v] = a.x; ar[4 * v + 1] = a.y; ar[4 * v + 2] = a.z; ar[4 * v + 3] = a.w;
+                    ai[4 * v] = c.x; ai[4 * v + 1] = c.y; ai[4 * v + 2] = c.z; ai[4 * v + 3] = c.w;
+                }
+            } else {
+                const float2 a = reinterpret_cast<const float2*>(gxr)[0];
+                const float2 c = reinterpret_cast<const float2*>(gxi)[0];
+                ar[0] = a.x; ar[1] = a.y;
+                ai[0] = c.x; ai[1] = c.y;
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < N; ++v) { ar[v] = 0.f; ai[v] = 0.f; }
+        }
+        float orr[N], oi[N];
+        auto ld = [&](int L, float& r, float& i) { r = ar[L]; i = ai[L]; };
+        auto st = [&](int k, float r, float i) { orr[k] = r; oi[k] = i; };
+        run_steps<S, ADJ>(t, w, ld, xw, xrd, twf, st, sync);
+        if (active) {
+            if constexpr (N >= 4) {
+#pragma unroll
+                for (int v = 0; v < N / 4; ++v) {
+                    reinterpret_cast<float4*>(gyr)[v] =
+                        make_float4(orr[4 * v], orr[4 * v + 1], orr[4 * v + 2], orr[4 * v + 3]);
+                    reinterpret_cast<float4*>(gyi)[v] =
+                        make_float4(oi[4 * v], oi[4 * v + 1], oi[4 * v + 2], oi[4 * v + 3]);
+                }
+            } else {
+                reinterpret_cast<float2*>(gyr)[0] = make_float2(orr[0], orr[1]);
+                reinterpret_cast<float2*>(gyi)[0] = make_float2(oi[0], oi[1]);
+            }
+        }
+    } else {
+        auto ld = [&](int L, float& r, float& i) {
+            if (active) { r = gxr[L]; i = gxi[L]; }
+            else { r = 0.f; i = 0.f; }
+        };
+        auto st = [&](int k, float r, float i) {
+            if (active) { gyr[k] = r; gyi[k] = i; }
+        };
+        run_steps<S, ADJ>(t, w, ld, xw, xrd, twf, st, sync);
+        if constexpr (S::NS > 1) sync();  // last reads done before the next tile writes
+    }
+}
 
+template <class CFG, bool ADJ>
+__global__ void __launch_bounds__(CFG::THREADS, CFG::MINB)
+k_rows(const float* xr, const float* xi, float* yr, float* yi, long long batch,
+       const float2* __restrict__ tw, const W64 w) {
+    using S = typename CFG::S;
+    extern __shared__ float4 smem4[];
+    float* const smem = reinterpret_cast<float*>(smem4);
+    const int t = (int)threadIdx.x & (S::T - 1);
+    const int g = (int)threadIdx.x >> S::LOGT;
+    float* const s_re = smem + g * CFG::BUF;
+    float* const s_im = s_re + CFG::PLANE;
     const long long ntiles = (batch + CFG::G - 1) / CFG::G;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long b = tile * CFG::G + g;
         const bool active = b < batch;
         const long long row = (active ? b : 0) * (long long)S::N;
-        const float* gxr = xr + row;
-        const float* gxi = xi + row;
-        float* gyr = yr + row;
-        float* gyi = yi + row;
-
-        if constexpr (S::T == 1) {
-            // whole row per thread: vector loads into registers, then the
-            // step engine reads them by compile-time index.
-            constexpr int N = S::N;
-            float ar[N], ai[N];
-            if (active) {
-                if constexpr (N >= 4) {
-#pragma unroll
-                    for (int v = 0; v < N / 4; ++v) {
-                        const float4 a = reinterpret_cast<const float4*>(gxr)[v];
-                        const float4 c = reinterpret_cast<const float4*>(gxi)[v];
-                        ar[4 * v] = a.x; ar[4 * v + 1] = a.y; ar[4 * v + 2] = a.z; ar[4 * v + 3] = a.w;
-                        ai[4 * v] = c.x; ai[4 * v + 1] = c.y; ai[4 * v + 2] = c.z; ai[4 * v + 3] = c.w;
-                    }
-                } else {
-                    const float2 a = reinterpret_cast<const float2*>(gxr)[0];
-                    const float2 c = reinterpret_cast<const float2*>(gxi)[0];
-                    ar[0] = a.x; ar[1] = a.y;
-                    ai[0] = c.x; ai[1] = c.y;
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < N; ++v) { ar[v] = 0.f; ai[v] = 0.f; }
-            }
-            float orr[N], oi[N];
-            auto ld = [&](int L, float& r, float& i) { r = ar[L]; i = ai[L]; };
-            auto st = [&](int k, float r, float i) { orr[k] = r; oi[k] = i; };
-            run_steps<S, ADJ>(t, w, ld, xw, xrd, twf, st, sync);
-            if (active) {
-                if constexpr (N >= 4) {
-#pragma unroll
-                    for (int v = 0; v < N / 4; ++v) {
-                        reinterpret_cast<float4*>(gyr)[v] =
-                            make_float4(orr[4 * v], orr[4 * v + 1], orr[4 * v + 2], orr[4 * v + 3]);
-                        reinterpret_cast<float4*>(gyi)[v] =
-                            make_float4(oi[4 * v], oi[4 * v + 1], oi[4 * v + 2], oi[4 * v + 3]);
-                    }
-                } else {
-                    reinterpret_cast<float2*>(gyr)[0] = make_float2(orr[0], orr[1]);
-                    reinterpret_cast<float2*>(gyi)[0] = make_float2(oi[0], oi[1]);
-                }
-            }
-        } else {
-            auto ld = [&](int L, float& r, float& i) {
-                if (active) { r = gxr[L]; i = gxi[L]; }
-                else { r = 0.f; i = 0.f; }
-            };
-            auto st = [&](int k, float r, float i) {
-                if (active) { gyr[k] = r; gyi[k] = i; }
-            };
-            run_steps<S, ADJ>(t, w, ld, xw, xrd, twf, st, sync);
-            if constexpr (S::NS > 1) sync();  // last reads done before the next tile writes
-        }
+        rows_tile<CFG, ADJ>(xr + row, xi + row, yr + row, yi + row, active, t, s_re, s_im, tw, w);
     }
 }
 

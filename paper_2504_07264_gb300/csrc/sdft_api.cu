@@ -13,8 +13,11 @@
 #include <new>
 #include <set>
 
+#include <vector>
+
 #include "../../include/sdft.h"
 #include "launch.h"
+#include "ragged.h"
 
 namespace sdft {
 const KernelInfo* rows_kernel_small(int logn);
@@ -51,6 +54,24 @@ struct HostStaging {
     float2* d_scratch = nullptr;       // second scratch set for the second slot
 };
 
+// State of a ragged plan: work order, work items and one CUDA graph per
+// direction (a memset of the work counter, then the persistent kernel).
+struct RaggedState {
+    bool on = false;
+    int64_t count = 0;
+    long long* d_offsets = nullptr;
+    int4* d_items = nullptr;
+    int nitems = 0;
+    int* d_counter = nullptr;
+    const float2* tw[17] = {};
+    unsigned classes = 0;              // bit l set: some transform has log2 N = l
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaGraphNode_t knode[2] = {nullptr, nullptr};
+    RaggedArgs args[2] = {};
+    std::mutex mu;
+};
+
 }  // namespace
 
 struct sdft_plan {
@@ -67,6 +88,7 @@ struct sdft_plan {
     int* d_status;
     W64 w64;
     HostStaging host;
+    RaggedState rag;
 };
 
 namespace {
@@ -98,6 +120,14 @@ void free_plan_memory(sdft_plan* p) {
     }
     if (p->host.start) cudaEventDestroy(p->host.start);
     if (p->host.d_scratch) cudaFree(p->host.d_scratch);
+    RaggedState& r = p->rag;
+    for (int d = 0; d < 2; ++d) {
+        if (r.exec[d]) cudaGraphExecDestroy(r.exec[d]);
+        if (r.graph[d]) cudaGraphDestroy(r.graph[d]);
+    }
+    if (r.d_offsets) cudaFree(r.d_offsets);
+    if (r.d_items) cudaFree(r.d_items);
+    if (r.d_counter) cudaFree(r.d_counter);
 }
 
 bool ranges_overlap(const void* a, const void* b, size_t bytes) {
@@ -151,6 +181,66 @@ int launch(const sdft_plan* p, int direction, const float* xr, const float* xi, 
     const long long tiles = (batch + p->kern->transforms_per_cta - 1) / p->kern->transforms_per_cta;
     if (scratch == nullptr && tiles < a.grid) a.grid = (int)std::max<long long>(tiles, 1);
     return p->kern->launch(a) == cudaSuccess ? SDFT_OK : SDFT_ERR_CUDA;
+}
+
+// Ragged plans: launch the direction's graph, building it on first use and
+// re-pointing its kernel node when the data pointers change.
+int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr,
+                  float* yi, cudaStream_t stream, float2* scratch) {
+    RaggedState& r = p->rag;
+    const int d = direction == SDFT_ADJOINT ? 1 : 0;
+    RaggedArgs a = {};
+    a.xr = xr;
+    a.xi = xi;
+    a.yr = yr;
+    a.yi = yi;
+    a.offsets = r.d_offsets;
+    a.items = r.d_items;
+    a.nitems = r.nitems;
+    a.counter = r.d_counter;
+    a.scratch = scratch;
+    for (int l = 0; l < 17; ++l) a.tw[l] = r.tw[l];
+    a.w = p->w64;
+    void* kargs[] = {&a};
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void*>(ragged_kernel_fn(d == 1));
+    kp.gridDim = dim3((unsigned)p->grid, 1, 1);
+    kp.blockDim = dim3((unsigned)ragged_threads(), 1, 1);
+    kp.sharedMemBytes = (unsigned)ragged_smem();
+    kp.kernelParams = kargs;
+    kp.extra = nullptr;
+    std::lock_guard<std::mutex> lk(r.mu);
+    if (!r.exec[d]) {
+        if (cudaGraphCreate(&r.graph[d], 0) != cudaSuccess) return SDFT_ERR_CUDA;
+        cudaMemsetParams mp = {};
+        mp.dst = r.d_counter;
+        mp.value = 0;
+        mp.elementSize = sizeof(int);
+        mp.width = 1;
+        mp.height = 1;
+        mp.pitch = 0;
+        cudaGraphNode_t mnode = nullptr;
+        if (cudaGraphAddMemsetNode(&mnode, r.graph[d], nullptr, 0, &mp) != cudaSuccess ||
+            cudaGraphAddKernelNode(&r.knode[d], r.graph[d], &mnode, 1, &kp) != cudaSuccess ||
+            cudaGraphInstantiate(&r.exec[d], r.graph[d], 0) != cudaSuccess) {
+            if (r.graph[d]) cudaGraphDestroy(r.graph[d]);
+            r.graph[d] = nullptr;
+            r.exec[d] = nullptr;
+            return SDFT_ERR_CUDA;
+        }
+        r.args[d] = a;
+    } else if (std::memcmp(&r.args[d], &a, sizeof(a)) != 0) {
+        if (cudaGraphExecKernelNodeSetParams(r.exec[d], r.knode[d], &kp) != cudaSuccess)
+            return SDFT_ERR_CUDA;
+        r.args[d] = a;
+    }
+    return cudaGraphLaunch(r.exec[d], stream) == cudaSuccess ? SDFT_OK : SDFT_ERR_CUDA;
+}
+
+int run(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr, float* yi,
+        cudaStream_t stream, long long batch, float2* scratch) {
+    if (p->rag.on) return launch_ragged(p, direction, xr, xi, yr, yi, stream, scratch);
+    return launch(p, direction, xr, xi, yr, yi, stream, batch, scratch);
 }
 
 }  // namespace
@@ -240,11 +330,116 @@ sdft_plan* sdft_plan_create(int64_t n, int64_t batch, int dtype) {
 }
 
 sdft_plan* sdft_plan_create_ragged(const int64_t* lengths, int64_t count, int dtype) {
-    (void)lengths;
-    (void)count;
-    (void)dtype;
-    fail(SDFT_ERR_UNSUPPORTED_N);
-    return nullptr;
+    if (lengths == nullptr || count < 1 || count > ((int64_t)1 << 31)) {
+        fail(SDFT_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    std::vector<int> logn((size_t)count);
+    int64_t total = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        const int l = log2_exact(lengths[t]);
+        if (l < 2 || l > kMaxLogN) { fail(SDFT_ERR_UNSUPPORTED_N); return nullptr; }
+        logn[(size_t)t] = l;
+        total += lengths[t];
+        if (total > ((int64_t)1 << 40)) { fail(SDFT_ERR_INVALID_ARG); return nullptr; }
+    }
+    if (dtype != SDFT_F32) { fail(SDFT_ERR_UNSUPPORTED_DTYPE); return nullptr; }
+
+    // work order: longest first (stable), items of per_item transforms
+    std::vector<long long> start((size_t)count);
+    {
+        long long o = 0;
+        for (int64_t t = 0; t < count; ++t) { start[(size_t)t] = o; o += lengths[t]; }
+    }
+    std::vector<long long> order_off;
+    std::vector<int4> items;
+    order_off.reserve((size_t)count);
+    unsigned classes = 0;
+    for (int l = kMaxLogN; l >= 2; --l) {
+        const int first = (int)order_off.size();
+        for (int64_t t = 0; t < count; ++t)
+            if (logn[(size_t)t] == l) order_off.push_back(start[(size_t)t]);
+        const int n_in = (int)order_off.size() - first;
+        if (n_in == 0) continue;
+        classes |= 1u << l;
+        const int per = ragged_class(l)->per_item;
+        for (int s0 = 0; s0 < n_in; s0 += per)
+            items.push_back(make_int4(l, first + s0, std::min(per, n_in - s0), 0));
+    }
+
+    sdft_plan* p = new (std::nothrow) sdft_plan();
+    if (!p) { fail(SDFT_ERR_ALLOC); return nullptr; }
+    p->magic = 0;
+    p->dtype = dtype;
+    p->n = 0;
+    p->batch = count;
+    p->points = total;
+    p->kern = nullptr;
+    RaggedState& r = p->rag;
+    r.on = true;
+    r.count = count;
+    r.nitems = (int)items.size();
+    r.classes = classes;
+    int status = SDFT_OK;
+    cudaStream_t st = nullptr;
+    do {
+        if (cudaGetDevice(&p->device) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+            status = SDFT_ERR_CUDA; break;
+        }
+        if (ragged_prepare() != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        p->grid = std::max(1, ragged_blocks_per_sm()) * sms;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            status = SDFT_ERR_CUDA; break;
+        }
+        int64_t tw_total = 64;
+        int64_t base[17] = {};
+        for (int l = 2; l <= kMaxLogN; ++l)
+            if (classes & (1u << l)) { base[l] = tw_total; tw_total += ragged_class(l)->tw_entries; }
+        if (cudaMalloc(&p->d_tw, tw_total * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&r.d_counter, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&r.d_offsets, order_off.size() * sizeof(long long)) != cudaSuccess ||
+            cudaMalloc(&r.d_items, items.size() * sizeof(int4)) != cudaSuccess) {
+            status = SDFT_ERR_ALLOC; break;
+        }
+        if (classes & ((1u << 15) | (1u << 16))) {
+            const size_t bytes = (size_t)p->grid * (size_t)ragged_scratch_per_cta() * sizeof(float2);
+            if (cudaMalloc(&p->d_scratch, bytes) != cudaSuccess) { status = SDFT_ERR_ALLOC; break; }
+        }
+        if (cudaMemsetAsync(p->d_status, 0, sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(r.d_counter, 0, sizeof(int), st) != cudaSuccess ||
+            cudaMemcpyAsync(r.d_offsets, order_off.data(), order_off.size() * sizeof(long long),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(r.d_items, items.data(), items.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            status = SDFT_ERR_CUDA; break;
+        }
+        if (make_w64(&p->w64, p->d_tw, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        for (int l = 2; l <= kMaxLogN && status == SDFT_OK; ++l) {
+            if (!(classes & (1u << l))) continue;
+            const RaggedClass* c = ragged_class(l);
+            r.tw[l] = p->d_tw + base[l];
+            if (make_tables(p->d_tw + base[l], c->tables, c->ntables, st) != cudaSuccess)
+                status = SDFT_ERR_CUDA;
+        }
+        if (status != SDFT_OK) break;
+        if (cudaStreamSynchronize(st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+    } while (0);
+    if (st) cudaStreamDestroy(st);
+    if (status != SDFT_OK) {
+        free_plan_memory(p);
+        delete p;
+        fail(status);
+        return nullptr;
+    }
+    p->magic = kMagic;
+    {
+        std::lock_guard<std::mutex> lk(g_registry_mu);
+        g_registry.insert(p);
+    }
+    return p;
 }
 
 void sdft_plan_destroy(sdft_plan* plan) {
@@ -270,7 +465,8 @@ int sdft_execute(const sdft_plan* plan, int direction, const float* xr, const fl
     if (s != SDFT_OK) return fail(s);
     s = check_device(plan);
     if (s != SDFT_OK) return fail(s);
-    s = launch(plan, direction, xr, xi, yr, yi, (cudaStream_t)stream, plan->batch, plan->d_scratch);
+    s = run(const_cast<sdft_plan*>(plan), direction, xr, xi, yr, yi, (cudaStream_t)stream,
+            plan->batch, plan->d_scratch);
     if (s != SDFT_OK) return fail(s);
     return SDFT_OK;
 }
@@ -294,21 +490,27 @@ int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const flo
     if (s != SDFT_OK) return fail(s);
     HostStaging& h = plan->host;
     const int64_t n = plan->n;
+    const bool rag = plan->rag.on;
     if (h.chunk == 0) {
-        // ~32 MiB per plane per slot, whole transforms, at least one
-        int64_t chunk = std::max<int64_t>(1, ((int64_t)32 << 20) / (n * (int64_t)sizeof(float)));
+        // ~32 MiB per plane per slot, whole transforms, at least one; a ragged
+        // plan moves its whole batch as one chunk
+        int64_t chunk = rag ? plan->batch
+                            : std::max<int64_t>(1, ((int64_t)32 << 20) / (n * (int64_t)sizeof(float)));
         chunk = std::min<int64_t>(chunk, plan->batch);
+        const int64_t chunk_points = rag ? plan->points : chunk * n;
         for (int sl = 0; sl < 2; ++sl) {
             for (int pl = 0; pl < 2; ++pl)
-                if (cudaMalloc(&h.d_buf[sl][pl], (size_t)chunk * n * sizeof(float)) != cudaSuccess)
+                if (cudaMalloc(&h.d_buf[sl][pl], (size_t)chunk_points * sizeof(float)) != cudaSuccess)
                     return fail(SDFT_ERR_ALLOC);
             if (cudaStreamCreateWithFlags(&h.streams[sl], cudaStreamNonBlocking) != cudaSuccess)
                 return fail(SDFT_ERR_CUDA);
         }
         if (cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming) != cudaSuccess)
             return fail(SDFT_ERR_CUDA);
-        if (plan->kern->scratch_per_cta > 0) {
-            const size_t sb = (size_t)plan->grid * (size_t)plan->kern->scratch_per_cta * sizeof(float2);
+        const int64_t scr = rag ? (plan->d_scratch ? ragged_scratch_per_cta() : 0)
+                                : plan->kern->scratch_per_cta;
+        if (scr > 0) {
+            const size_t sb = (size_t)plan->grid * (size_t)scr * sizeof(float2);
             if (cudaMalloc(&h.d_scratch, sb) != cudaSuccess) return fail(SDFT_ERR_ALLOC);
         }
         h.chunk = chunk;
@@ -323,13 +525,14 @@ int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const flo
         cudaStream_t st = h.streams[sl];
         const int64_t b0 = c * h.chunk;
         const int64_t nb = std::min<int64_t>(h.chunk, plan->batch - b0);
-        const size_t off = (size_t)b0 * n, bytes = (size_t)nb * n * sizeof(float);
+        const size_t off = rag ? 0 : (size_t)b0 * n;
+        const size_t bytes = (rag ? (size_t)plan->points : (size_t)nb * n) * sizeof(float);
         float* dr = h.d_buf[sl][0];
         float* di = h.d_buf[sl][1];
         if (cudaMemcpyAsync(dr, xr + off, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemcpyAsync(di, xi + off, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return fail(SDFT_ERR_CUDA);
-        s = launch(plan, direction, dr, di, dr, di, st, nb, sl == 0 ? plan->d_scratch : h.d_scratch);
+        s = run(plan, direction, dr, di, dr, di, st, nb, sl == 0 ? plan->d_scratch : h.d_scratch);
         if (s != SDFT_OK) return fail(s);
         if (cudaMemcpyAsync(yr + off, dr, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(yi + off, di, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -360,11 +563,25 @@ int sdft_plan_dtype(const sdft_plan* plan) { return plan_alive(plan) ? plan->dty
 
 int sdft_plan_launches(const sdft_plan* plan, int direction) {
     (void)direction;
-    return plan_alive(plan) ? plan->kern->launches : 0;
+    if (!plan_alive(plan)) return 0;
+    return plan->rag.on ? 1 : plan->kern->launches;
 }
 
 int sdft_plan_describe(const sdft_plan* plan, char* buf, int64_t len) {
     if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN), -1;
+    if (plan->rag.on) {
+        char cls[128] = {0};
+        int o = 0;
+        for (int l = 2; l <= kMaxLogN; ++l)
+            if (plan->rag.classes & (1u << l))
+                o += std::snprintf(cls + o, sizeof(cls) - (size_t)o, "%s%d", o ? "," : "", 1 << l);
+        return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
+                             "ragged: %lld transforms, %lld points, lengths {%s}; one persistent "
+                             "launch (graph: counter memset + kernel), %d threads/CTA, %zu B smem, "
+                             "grid %d, %d work items",
+                             (long long)plan->rag.count, (long long)plan->points, cls,
+                             ragged_threads(), ragged_smem(), plan->grid, plan->rag.nitems);
+    }
     return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
                          "%s; %d threads/CTA, %zu B smem, grid %d, %d transform(s)/CTA tile",
                          plan->kern->name, plan->kern->threads, plan->kern->smem, plan->grid,

@@ -1,0 +1,160 @@
+"""Ragged batches (GPU): mixed power-of-two lengths in one persistent launch
+replayed from a CUDA graph, checked against the CPU oracle per transform."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import TOL_F32, rel_l2_rows
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2504_07264_gb300 import build
+    build.build()
+    O.build()
+
+
+def _ragged_inputs(lengths, seed):
+    rng = np.random.default_rng(seed)
+    total = int(np.sum(lengths))
+    xr = rng.standard_normal(total).astype(np.float32)
+    xi = rng.standard_normal(total).astype(np.float32)
+    off = np.zeros(len(lengths) + 1, dtype=np.int64)
+    np.cumsum(lengths, out=off[1:])
+    return xr, xi, off
+
+
+def _run(plan, xr, xi, direction, out=None):
+    import torch
+    dxr = torch.from_numpy(xr).cuda()
+    dxi = torch.from_numpy(xi).cuda()
+    if out is None:
+        yr, yi = plan.execute(direction, dxr, dxi)
+    else:
+        yr, yi = plan.execute(direction, dxr, dxi, *out)
+    torch.cuda.synchronize()
+    return yr.cpu().numpy(), yi.cpu().numpy()
+
+
+def _check_segments(lengths, off, xr, xi, yr, yi, direction, which=None):
+    fn = O.dft_factored_dit if direction == 0 else O.adjoint_factored
+    idx = range(len(lengths)) if which is None else which
+    worst = 0.0
+    for t in idx:
+        a, b = off[t], off[t + 1]
+        rr, ri = fn(xr[a:b][None, :], xi[a:b][None, :])
+        e = rel_l2_rows(yr[a:b][None, :], yi[a:b][None, :], rr, ri).max()
+        worst = max(worst, e)
+    return worst
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_mixed_lengths_match_oracle(direction):
+    from paper_2504_07264_gb300 import Plan
+    rng = np.random.default_rng(40)
+    lengths = (1 << rng.integers(2, 17, size=70)).astype(np.int64)
+    lengths[:3] = [65536, 4, 32768]          # both two-pass classes and the smallest
+    xr, xi, off = _ragged_inputs(lengths, 41 + direction)
+    with Plan(lengths=lengths) as plan:
+        assert plan.launches() == 1
+        yr, yi = _run(plan, xr, xi, direction)
+    assert _check_segments(lengths, off, xr, xi, yr, yi, direction) <= TOL_F32
+
+
+def test_every_class_and_many_items():
+    """Every length 4..65536, several work items per class, ragged counts."""
+    from paper_2504_07264_gb300 import Plan
+    lengths = []
+    for logn in range(2, 17):
+        reps = max(1, 3000 >> logn) + logn % 3
+        lengths += [1 << logn] * reps
+    lengths = np.random.default_rng(5).permutation(np.array(lengths, dtype=np.int64))
+    xr, xi, off = _ragged_inputs(lengths, 43)
+    with Plan(lengths=lengths) as plan:
+        yr, yi = _run(plan, xr, xi, 0)
+    pick = np.random.default_rng(6).choice(len(lengths), 80, replace=False)
+    big = [t for t in range(len(lengths)) if lengths[t] >= 16384]
+    assert _check_segments(lengths, off, xr, xi, yr, yi, 0, sorted(set(pick) | set(big))) <= TOL_F32
+
+
+def test_matches_uniform_plans_bitwise():
+    """A ragged plan computes each transform exactly as the uniform plan of its
+    length does (same radix schedule and tables)."""
+    from paper_2504_07264_gb300 import Plan
+    for n, cnt in ((16, 700), (1024, 37), (4096, 9), (65536, 3)):
+        lengths = np.full(cnt, n, dtype=np.int64)
+        xr, xi, _ = _ragged_inputs(lengths, 44)
+        with Plan(lengths=lengths) as rp:
+            a = _run(rp, xr, xi, 0)
+        with Plan(n, cnt) as up:
+            b = _run(up, xr.reshape(cnt, n), xi.reshape(cnt, n), 0)
+        assert np.array_equal(a[0], b[0].ravel()) and np.array_equal(a[1], b[1].ravel()), n
+
+
+def test_graph_replay_with_new_buffers():
+    import torch
+
+    from paper_2504_07264_gb300 import Plan
+    lengths = np.array([8, 1024, 65536, 64, 4096, 16], dtype=np.int64)
+    xr, xi, off = _ragged_inputs(lengths, 45)
+    with Plan(lengths=lengths) as plan:
+        first = _run(plan, xr, xi, 0)
+        out = (torch.empty(xr.size, device="cuda"), torch.empty(xr.size, device="cuda"))
+        second = _run(plan, xr, xi, 0, out=out)     # new input and output pointers
+        third = _run(plan, xr, xi, 0)               # and back
+    for r in (second, third):
+        assert np.array_equal(first[0], r[0]) and np.array_equal(first[1], r[1])
+    assert _check_segments(lengths, off, xr, xi, *first, 0) <= TOL_F32
+
+
+def test_in_place_and_host_buffers():
+    import torch
+
+    from paper_2504_07264_gb300 import Plan
+    lengths = np.array([65536, 8, 2048, 32768, 4], dtype=np.int64)
+    xr, xi, off = _ragged_inputs(lengths, 46)
+    with Plan(lengths=lengths) as plan:
+        ref = _run(plan, xr, xi, 1)
+        dxr = torch.from_numpy(xr).cuda()
+        dxi = torch.from_numpy(xi).cuda()
+        plan.execute(1, dxr, dxi, dxr, dxi)
+        torch.cuda.synchronize()
+        assert np.array_equal(dxr.cpu().numpy(), ref[0]) and np.array_equal(dxi.cpu().numpy(), ref[1])
+        hyr = np.empty_like(xr)
+        hyi = np.empty_like(xi)
+        plan.execute_host(1, xr, xi, hyr, hyi)
+        assert np.array_equal(hyr, ref[0]) and np.array_equal(hyi, ref[1])
+
+
+def test_full_ragged_workload_sampled():
+    """10000 transforms, lengths 2^U{3..16} (seed 4): sampled transforms of every
+    length against the oracle, Parseval on every transform."""
+    import torch
+
+    from paper_2504_07264_gb300 import Plan
+    lengths, off, xr, xi = W.ragged_planes()
+    assert int(off[-1]) == 96714152
+    with Plan(lengths=lengths) as plan:
+        dxr = torch.from_numpy(xr).cuda()
+        dxi = torch.from_numpy(xi).cuda()
+        yr, yi = plan.forward(dxr, dxi)
+        seg = torch.repeat_interleave(torch.arange(len(lengths), device="cuda"),
+                                      torch.from_numpy(lengths).cuda())
+        e_in = torch.zeros(len(lengths), dtype=torch.float64, device="cuda").index_add_(
+            0, seg, dxr.double() ** 2 + dxi.double() ** 2) * torch.from_numpy(lengths).cuda()
+        e_out = torch.zeros(len(lengths), dtype=torch.float64, device="cuda").index_add_(
+            0, seg, yr.double() ** 2 + yi.double() ** 2)
+        parseval = ((e_out - e_in).abs() / e_in).max().item()
+        hy = (yr.cpu().numpy(), yi.cpu().numpy())
+    assert parseval < 1e-5
+    rng = np.random.default_rng(7)
+    pick = []
+    for logn in range(3, 17):
+        cand = np.nonzero(lengths == (1 << logn))[0]
+        pick += list(rng.choice(cand, min(2, cand.size), replace=False))
+    assert _check_segments(lengths, off, xr, xi, *hy, 0, sorted(pick)) <= TOL_F32
