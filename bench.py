@@ -287,25 +287,32 @@ def run_ours(args) -> None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_fwd, ms_adj = t.tolist()
 
-    # end to end through the C ABI on pinned host buffers
+    # end to end through the C ABI on pinned host buffers: the default mode
+    # (zero copy for page-locked buffers) and the staged copy pipeline
     e2e_s = None
+    e2e_modes = {}
     if not args.no_e2e:
+        from paper_2504_07264_gb300.sdft import SDFT_HOST_STAGED, SDFT_HOST_ZERO_COPY
         hxr = torch.from_numpy(xr_h).pin_memory()
         hxi = torch.from_numpy(xi_h).pin_memory()
         hyr = torch.empty_like(hxr).pin_memory()
         hyi = torch.empty_like(hxi).pin_memory()
         e2e_steps = max(1, min(args.steps, 10))
-        plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)   # allocates staging once
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)
-        barrier()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = t.item()
+        for mode_name, mode in (("staged", SDFT_HOST_STAGED), ("zero_copy", SDFT_HOST_ZERO_COPY)):
+            plan.set_host_mode(mode)
+            plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)   # first call sets up
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)
+            barrier()
+            sec = (time.perf_counter() - t0) / e2e_steps
+            if dist is not None:
+                t = torch.tensor([sec], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                sec = t.item()
+            e2e_modes[mode_name] = sec
+        e2e_s = e2e_modes["zero_copy"]
     describe = plan.describe()
     plan.destroy()
 
@@ -350,7 +357,10 @@ def run_ours(args) -> None:
         "e2e": None if e2e_s is None else {
             "value": world * points / e2e_s / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": 2 * points * 4, "d2h_bytes_per_step": 2 * points * 4,
-            "api": "sdft_execute_host (pinned host buffers)"},
+            "api": "sdft_execute_host, pinned host buffers, default mode (zero copy: the kernel "
+                   "reads and writes host memory over NVLink-C2C)",
+            "staged_pipeline": {"value": world * points / e2e_modes["staged"] / 1e9,
+                                "unit": UNIT}},
         "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -361,8 +371,12 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
-def _measure_uniform(n: int, batch: int, xr_h, xi_h, steps: int, warmup: int, stream) -> dict:
-    """Forward and adjoint kernel times of one uniform plan (one GPU)."""
+def _measure_uniform(n: int, batch: int, xr_h, xi_h, steps: int, warmup: int, stream,
+                     dtype: int = 0, accuracy_sample: int = 0) -> dict:
+    """Forward and adjoint kernel times of one uniform plan (one GPU); with
+    accuracy_sample > 0 also the relative L2 error of that many sampled
+    transforms against the CPU oracle."""
+    import numpy as np
     import torch
 
     from paper_2504_07264_gb300 import SDFT_ADJOINT, SDFT_FORWARD, Plan
@@ -372,7 +386,21 @@ def _measure_uniform(n: int, batch: int, xr_h, xi_h, steps: int, warmup: int, st
     yi = torch.empty_like(xi)
     points = n * batch
     peak = _peaks()["hbm_gbs"]
-    with Plan(n, batch) as plan:
+    acc = None
+    with Plan(n, batch, dtype) as plan:
+        if accuracy_sample:
+            from oracle import oracle
+            plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)
+            idx = np.sort(np.random.default_rng(8).choice(batch, accuracy_sample, replace=False))
+            sel = torch.from_numpy(idx).cuda()
+            gr = yr.index_select(0, sel).cpu().numpy().astype(np.float64)
+            gi = yi.index_select(0, sel).cpu().numpy().astype(np.float64)
+            rr, ri = oracle.dft_factored_dit(xr_h[idx], xi_h[idx])
+            rows = np.sqrt(((gr - rr) ** 2 + (gi - ri) ** 2).sum(1) / (rr ** 2 + ri ** 2).sum(1))
+            acc = {"rel_l2": float(np.sqrt(((gr - rr) ** 2 + (gi - ri) ** 2).sum()
+                                           / (rr ** 2 + ri ** 2).sum())),
+                   "rel_l2_worst_transform": float(rows.max()),
+                   "sample": f"{accuracy_sample} transforms vs the float64 oracle"}
         fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
         adj = lambda: plan.execute(SDFT_ADJOINT, xr, xi, yr, yi, stream)  # noqa: E731
         for _ in range(warmup):
@@ -381,8 +409,10 @@ def _measure_uniform(n: int, batch: int, xr_h, xi_h, steps: int, warmup: int, st
         torch.cuda.synchronize()
         ms_f = _time_steps(fwd, steps, stream)
         ms_a = _time_steps(adj, steps, stream)
-        out = {"n": n, "batch": batch, "schedule": plan.describe(),
+        out = {"n": n, "batch": batch, "dtype": dtype, "schedule": plan.describe(),
                "launches_per_call": plan.launches(SDFT_FORWARD)}
+        if acc is not None:
+            out["accuracy"] = acc
     for name, ms in (("forward", ms_f), ("adjoint", ms_a)):
         gbs = BYTES_PER_POINT * points / (ms * 1e-3) / 1e9
         out[name] = {"gpts": points / (ms * 1e-3) / 1e9, "ms": ms, "gbs": gbs, "frac": gbs / peak}
@@ -430,9 +460,20 @@ def run_workload(args) -> None:
         cfg = workloads.PRECISION
         n, batch = cfg["n"], cfg["batch"]
         xr_h, xi_h = workloads.precision()
-        line.update(_measure_uniform(n, batch, xr_h, xi_h, args.steps, args.warmup, stream))
-        line["metric"] = "planar DFT Gpts/s, N=256 B=262144 (FP32 path)"
-        line["value"] = line["forward"]["gpts"]
+        paths = {}
+        for name, dt in (("f32", 0), ("split_bf16", 1), ("split_fp16", 2)):
+            paths[name] = _measure_uniform(n, batch, xr_h, xi_h, args.steps, args.warmup, stream,
+                                           dtype=dt, accuracy_sample=256)
+        del xr_h, xi_h
+        # the bandwidth workload's shape on the split-BF16 path as well
+        br, bi = workloads.bandwidth()
+        for name, dt in (("f32_n1024", 0), ("split_bf16_n1024", 1), ("split_fp16_n1024", 2)):
+            paths[name] = _measure_uniform(1024, 65536, br, bi, args.steps, args.warmup, stream,
+                                           dtype=dt, accuracy_sample=64)
+        line["paths"] = paths
+        line["metric"] = ("planar DFT Gpts/s, N=256 B=262144 |x| log-uniform: FP32 vs split-BF16 vs "
+                          "split-FP16 tensor cores (and N=1024 B=65536)")
+        line["value"] = paths["split_bf16"]["forward"]["gpts"]
     elif args.workload == "ragged":
         from paper_2504_07264_gb300 import SDFT_ADJOINT, SDFT_FORWARD, Plan
         lengths, off, xr_h, xi_h = workloads.ragged_planes()

@@ -121,18 +121,49 @@ SDFT_API int sdft_adjoint(const sdft_plan* plan, const float* xr, const float* x
 SDFT_API int sdft_execute(const sdft_plan* plan, int direction, const float* xr, const float* xi,
                  float* yr, float* yi, void* stream);
 
-/* The same transform on HOST buffers: copies xr, xi to plan-owned device
- * staging buffers, transforms, and copies the result back to yr, yi, in
- * chunks pipelined over the plan's internal streams; returns after the
- * result is in yr, yi.  Host buffers should be page-locked for full speed.
- * The staging buffers (a few chunks, not the whole batch) are allocated by the
- * first host call on a plan.  `stream`: work is ordered after prior work on it. */
+/* The same transform on HOST buffers; returns after the result is in yr, yi.
+ * Two ways, chosen by sdft_plan_set_host_mode:
+ *   zero copy (default when all four buffers are page-locked host memory the
+ *     GPU can address, e.g. from cudaHostAlloc): the kernel reads xr, xi and
+ *     writes yr, yi directly over the CPU-GPU link, on `stream`;
+ *   staged (otherwise): xr, xi are copied to plan-owned device staging
+ *     buffers, transformed, and copied back, in chunks pipelined over the
+ *     plan's two internal streams, ordered after prior work on `stream`.  The
+ *     staging buffers (two chunks of ~32 MiB per plane, not the whole batch)
+ *     are allocated by the first staged call on a plan. */
 SDFT_API int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const float* xi,
                       float* yr, float* yi, void* stream);
+
+#define SDFT_HOST_AUTO      0   /* zero copy if every buffer is page-locked, else staged */
+#define SDFT_HOST_STAGED    1   /* always staged */
+#define SDFT_HOST_ZERO_COPY 2   /* always zero copy (SDFT_ERR_INVALID_ARG if impossible) */
+/* Choose how sdft_execute_host moves data (default SDFT_HOST_AUTO). */
+SDFT_API int sdft_plan_set_host_mode(sdft_plan* plan, int mode);
 
 /* Wait for `stream`, then read and clear the plan's device status word:
  * SDFT_OK, or SDFT_ERR_TIMEOUT if a bounded device-side wait gave up. */
 SDFT_API int sdft_plan_sync_status(const sdft_plan* plan, void* stream);
+
+/* ---- schedules and autotuning ------------------------------------------- */
+/* Each length has one or more compiled schedules (radix split, threads per
+ * transform, transforms per CTA, register-DFT order).  sdft_plan_create uses
+ * the schedule currently selected for its length (index 0 until something is
+ * selected); the selection is process-wide and affects plans created later.
+ * Functions returning a count or index return a negative status on error. */
+SDFT_API int sdft_schedule_count(int64_t n, int dtype);
+/* Describe schedule `index` of length n into buf (snprintf convention). */
+SDFT_API int sdft_schedule_describe(int64_t n, int dtype, int index, char* buf, int64_t len);
+/* Select schedule `index` for length n (SDFT_OK, or SDFT_ERR_INVALID_ARG). */
+SDFT_API int sdft_schedule_select(int64_t n, int dtype, int index);
+SDFT_API int sdft_schedule_selected(int64_t n, int dtype);
+/* Time every schedule of length n on the caller's device buffers (`batch`
+ * transforms, forward, `reps` timed launches after two warm-up launches, CUDA
+ * events on `stream`), write the mean milliseconds per launch of schedule i to
+ * ms_out[i] (may be NULL; room for sdft_schedule_count entries), select the
+ * fastest and return its index.  Creates and destroys one temporary plan per
+ * schedule, so it allocates device memory and synchronises `stream`. */
+SDFT_API int sdft_autotune(int64_t n, int64_t batch, int dtype, const float* xr, const float* xi,
+                           float* yr, float* yi, int reps, float* ms_out, void* stream);
 
 /* ---- allocation-free long transforms ---------------------------------- */
 /* The paper has no counterpart to this entry point.

@@ -1,0 +1,147 @@
+"""Autotuner for the per-length schedules of libsdft.so.
+
+Every transform length has one or more compiled schedules (radix split,
+threads per transform, transforms per CTA, register-DFT order).  ``tune``
+times each of them on the GPU through the C ABI's ``sdft_autotune`` (CUDA
+events, the caller's buffers) and records the fastest; ``apply`` selects the
+recorded schedules for the plans created afterwards.  Results are kept as JSON
+keyed by GPU name, dtype and N:
+
+    {"NVIDIA GB300": {"0": {"1024": {"index": 0, "ms": [...], "schedules": [...]}}}}
+
+At import of the package nothing is changed; ``ensure_applied()`` (called by
+``Plan``) loads the file named by the environment variable SDFT_TUNE_CACHE, or
+else the table shipped with the package (``tuned_schedules.json``), once.
+
+CLI:  python -m paper_2504_07264_gb300.autotune [--out FILE] [--points P] [--reps R]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import threading
+
+from . import sdft as S
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SHIPPED = os.path.join(HERE, "tuned_schedules.json")
+
+_applied = False
+_lock = threading.Lock()
+
+
+def gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def tune_one(n: int, dtype: int = S.SDFT_F32, points: int = 1 << 24, reps: int = 20,
+             stream=None) -> dict:
+    """Time every schedule of length n on ``points`` complex values of random
+    data (forward); selects the fastest and returns its record."""
+    import ctypes
+
+    import torch
+    batch = max(1, points // n)
+    count = S.sdft_schedule_count(n, dtype)
+    if count < 0:
+        raise S.SdftError(-count, f"sdft_schedule_count({n})")
+    g = torch.Generator(device="cuda").manual_seed(n)
+    xr = torch.randn(batch * n, device="cuda", generator=g)
+    xi = torch.randn(batch * n, device="cuda", generator=g)
+    yr = torch.empty_like(xr)
+    yi = torch.empty_like(xi)
+    ms = (ctypes.c_float * count)()
+    st = int((stream or torch.cuda.current_stream()).cuda_stream)
+    best = S.sdft_autotune(n, batch, dtype, xr.data_ptr(), xi.data_ptr(), yr.data_ptr(),
+                           yi.data_ptr(), reps, ctypes.addressof(ms), st)
+    if best < 0:
+        raise S.SdftError(-best, f"sdft_autotune({n})")
+    return {"index": int(best), "ms": [float(v) for v in ms], "batch": batch,
+            "schedules": [S.sdft_schedule_describe(n, dtype, i) for i in range(count)]}
+
+
+def tune(sizes=None, dtype: int = S.SDFT_F32, points: int = 1 << 24, reps: int = 20) -> dict:
+    """Tune every length in ``sizes`` (default 2 .. 65536); returns the table
+    for this GPU: {str(dtype): {str(n): record}}."""
+    sizes = [1 << m for m in range(1, 17)] if sizes is None else sizes
+    out = {}
+    for n in sizes:
+        if S.sdft_schedule_count(n, dtype) <= 1:
+            continue
+        out[str(n)] = tune_one(n, dtype, points, reps)
+    return {str(dtype): out}
+
+
+def apply(table: dict, name: str | None = None) -> int:
+    """Select the recorded schedules of GPU ``name`` (default: the current
+    one); returns how many lengths were set."""
+    if name is None:
+        name = gpu_name()
+    applied = 0
+    for dtype, per_n in table.get(name, {}).items():
+        for n, rec in per_n.items():
+            idx = int(rec["index"])
+            if idx < S.sdft_schedule_count(int(n), int(dtype)) and \
+                    S.sdft_schedule_select(int(n), int(dtype), idx) == S.SDFT_OK:
+                applied += 1
+    return applied
+
+
+def load(path: str) -> dict:
+    with open(path) as f:
+        return json.load(f)
+
+
+def save(table: dict, path: str, name: str | None = None) -> None:
+    """Merge this GPU's ``table`` into the JSON file at ``path``."""
+    if name is None:
+        name = gpu_name()
+    full = load(path) if os.path.exists(path) else {}
+    mine = full.setdefault(name, {})
+    for dtype, per_n in table.items():
+        mine.setdefault(dtype, {}).update(per_n)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(full, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def ensure_applied() -> None:
+    """Apply the tuning file once per process (SDFT_TUNE_CACHE, else the
+    shipped table); silently does nothing if neither exists."""
+    global _applied
+    with _lock:
+        if _applied:
+            return
+        _applied = True
+        path = os.environ.get("SDFT_TUNE_CACHE") or SHIPPED
+        if os.path.exists(path):
+            try:
+                apply(load(path))
+            except Exception:
+                pass
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description="time every schedule and record the fastest")
+    ap.add_argument("--out", default=os.environ.get("SDFT_TUNE_CACHE") or SHIPPED)
+    ap.add_argument("--points", type=int, default=1 << 24)
+    ap.add_argument("--reps", type=int, default=20)
+    a = ap.parse_args(argv)
+    from . import build
+    build.build()
+    table = tune(points=a.points, reps=a.reps)
+    save(table, a.out)
+    for dtype, per_n in table.items():
+        for n, rec in sorted(per_n.items(), key=lambda kv: int(kv[0])):
+            times = ", ".join(f"{t * 1e3:.1f}" for t in rec["ms"])
+            print(f"N={n:>6}: best {rec['index']}  (us/launch: {times})")
+    print(f"wrote {a.out}")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -114,6 +114,34 @@ __device__ __forceinline__ void dft_regs(float (&re)[E], float (&im)[E], const i
     }
 }
 
+// In-register R-point DFT in the order of Eq. (6): the input must sit in
+// bit-reversed register order (S of Eq. (6), a compile-time renaming done by
+// the caller); then for i = 1..log2 R the rotation D(i) (omega^(i,q) on the
+// lower half of every block of 2^i points) and the butterfly W(i) (sum and
+// difference of the halves).  Output bin d lands in register off + d.
+template <int R, bool ADJ, int E>
+__device__ __forceinline__ void dft_regs_dit(float (&re)[E], float (&im)[E], const int off,
+                                             const W64& w) {
+#pragma unroll
+    for (int span = 1; span < R; span <<= 1) {
+#pragma unroll
+        for (int base = 0; base < R; base += 2 * span) {
+#pragma unroll
+            for (int q = 0; q < span; ++q) {
+                const int a = off + base + q;
+                const int b = a + span;
+                float vr = re[b], vi = im[b];
+                rot_const<ADJ>(vr, vi, q, 2 * span, w);       // D(i)
+                const float ur = re[a], ui = im[a];
+                re[a] = ur + vr;                              // W(i)
+                im[a] = ui + vi;
+                re[b] = ur - vr;
+                im[b] = ui - vi;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Step engine.  A sub-DFT of size N = 2^LOGN is run by T = N / E cooperating
 // threads (E = 2^LOGE elements each) in up to three steps of radix
@@ -137,8 +165,13 @@ __device__ __forceinline__ void dft_regs(float (&re)[E], float (&im)[E], const i
 //   sync()               barrier over the T threads of this sub-DFT (and
 //                        every other sub-DFT sharing its exchange buffer)
 // ---------------------------------------------------------------------------
-template <int LOGN_, int LOGE_, int LR0, int LR1, int LR2>
+template <int LOGN_, int LOGE_, int LR0, int LR1, int LR2, bool DIT_ = false>
 struct Steps {
+    // DIT: the register DFTs of every step run in the order of Eq. (6)
+    // (bit-reversed gather, rotation then butterfly); otherwise decimation in
+    // frequency (butterfly then rotation, bit-reversed result).  Same values
+    // up to rounding order.
+    static constexpr bool DIT = DIT_;
     static constexpr int LOGN = LOGN_, N = 1 << LOGN;
     static constexpr int LOGE = LOGE_, E = 1 << LOGE;
     static constexpr int LOGT = LOGN - LOGE, T = 1 << LOGT;
@@ -173,8 +206,9 @@ __device__ __forceinline__ void step_gather(float (&re)[S::E], float (&im)[S::E]
 #pragma unroll
         for (int i = 0; i < K::R; ++i) {
             const int L = t + S::T * f + K::C * i;
-            if constexpr (s == 0) ld(L, re[f * K::R + i], im[f * K::R + i]);
-            else xr(L, re[f * K::R + i], im[f * K::R + i]);
+            const int reg = f * K::R + (S::DIT ? brevc(i, K::LR) : i);
+            if constexpr (s == 0) ld(L, re[reg], im[reg]);
+            else xr(L, re[reg], im[reg]);
         }
 }
 
@@ -184,7 +218,10 @@ __device__ __forceinline__ void step_compute_scatter(float (&re)[S::E], float (&
                                                      ST& st) {
     using K = StepK<S, s>;
 #pragma unroll
-    for (int f = 0; f < K::F; ++f) dft_regs<K::R, ADJ>(re, im, f * K::R, w);
+    for (int f = 0; f < K::F; ++f) {
+        if constexpr (S::DIT) dft_regs_dit<K::R, ADJ>(re, im, f * K::R, w);
+        else dft_regs<K::R, ADJ>(re, im, f * K::R, w);
+    }
 #pragma unroll
     for (int f = 0; f < K::F; ++f) {
         const int c = t + S::T * f;
@@ -192,7 +229,7 @@ __device__ __forceinline__ void step_compute_scatter(float (&re)[S::E], float (&
         const int nl = c >> K::LP;
 #pragma unroll
         for (int d = 0; d < K::R; ++d) {
-            const int reg = f * K::R + brevc(d, K::LR);
+            const int reg = f * K::R + (S::DIT ? d : brevc(d, K::LR));
             if constexpr (K::LAST) {
                 st(lo + K::P * d, re[reg], im[reg]);
             } else {

@@ -16,7 +16,8 @@ struct LargeCfg {
     static constexpr int TS1 = 32 * (WARPS / SA::T);   // columns per pass-1 tile
     static constexpr int TS2 = 32 * (WARPS / SC::T);   // rows per pass-2 tile
     static_assert(C % TS1 == 0 && A % TS2 == 0, "tiles");
-    static constexpr int P1_FLOATS = 2 * A * TS1;
+    static constexpr int P1_TILE = 2 * A * TS1;             // one tile, both planes
+    static constexpr int P1_FLOATS = 3 * P1_TILE;           // two prefetch buffers + exchange
     static constexpr int STG = C + 1;                  // padded staging row
     static constexpr int P2_STAGE = 2 * TS2 * STG;
     static constexpr int P2_FLOATS = P2_STAGE + 2 * C * TS2;
@@ -25,6 +26,19 @@ struct LargeCfg {
     // twiddle tables: A-DFT step 0, C-DFT step 0, then W_N^{col * d}
     static constexpr int64_t TWA = 0, TWC = A, TWB = A + C, TW_TOTAL = A + C + (int64_t)N;
 };
+
+// 16-byte asynchronous global -> shared copy (no register staging).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" :: "n"(PENDING) : "memory");
+}
 
 // One whole transform of CFG by the calling CTA (all CFG::THREADS threads):
 // pass 1 into the CTA's scratch slot, pass 2 to the output.  `sm` is the
@@ -41,16 +55,42 @@ __device__ __forceinline__ void large_one(const float* gxr, const float* gxi, fl
     const int warp = (int)threadIdx.x >> 5;
     auto sync = [] { __syncthreads(); };
     // ---------------- pass 1: A-point DFTs down the columns ------------
+    // Column tiles (A rows x TS1 columns, both planes) are copied into one
+    // of two shared buffers with cp.async while the previous tile is being
+    // transformed, so the HBM reads overlap the register DFTs.
     {
         const int ta = warp % SA::T;
         const int sub = (warp / SA::T) * 32 + lane;
-        float* const x_re = sm;
-        float* const x_im = sm + A * CFG::TS1;
-        for (int tile = 0; tile < C / CFG::TS1; ++tile) {
+        constexpr int TILES = C / CFG::TS1;
+        constexpr int CHUNKS = A * CFG::TS1 / 4;         // 16-byte chunks per plane
+        float* const x_re = sm + 2 * CFG::P1_TILE;       // exchange
+        float* const x_im = x_re + A * CFG::TS1;
+        auto issue = [&](int tile) {
+            float* const buf = sm + (tile & 1) * CFG::P1_TILE;
+            const int col0 = tile * CFG::TS1;
+            for (int u = (int)threadIdx.x; u < CHUNKS; u += CFG::THREADS) {
+                const int L = u / (CFG::TS1 / 4), q = u % (CFG::TS1 / 4);
+                cp_async16(buf + L * CFG::TS1 + 4 * q, gxr + col0 + 4 * q + (long long)C * L);
+                cp_async16(buf + A * CFG::TS1 + L * CFG::TS1 + 4 * q,
+                           gxi + col0 + 4 * q + (long long)C * L);
+            }
+            cp_async_commit();
+        };
+        issue(0);
+        for (int tile = 0; tile < TILES; ++tile) {
+            if (tile + 1 < TILES) {
+                issue(tile + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            sync();                                      // this tile's copies visible
+            const float* const b_re = sm + (tile & 1) * CFG::P1_TILE;
+            const float* const b_im = b_re + A * CFG::TS1;
             const int col = tile * CFG::TS1 + sub;
             auto ld = [&](int L, float& r, float& i) {
-                r = gxr[col + C * L];
-                i = gxi[col + C * L];
+                r = b_re[L * CFG::TS1 + sub];
+                i = b_im[L * CFG::TS1 + sub];
             };
             auto xw = [&](int L, float r, float i) {
                 x_re[L * CFG::TS1 + sub] = r;
@@ -69,7 +109,7 @@ __device__ __forceinline__ void large_one(const float* gxr, const float* gxi, fl
                 scr_im[k * C + col] = i;
             };
             run_steps<SA, ADJ>(ta, w, ld, xw, xrd, twf, st, sync);
-            sync();
+            sync();                                      // buffer and exchange free again
         }
     }
     // scratch writes of pass 1 visible to the whole CTA (the last sync above)

@@ -19,9 +19,10 @@
 
 namespace sdft {
 
-template <int LOGN, int LOGE, int LR0, int LR1, int LR2, int G_, int SBX_ = 0, int MINB_ = 1>
+template <int LOGN, int LOGE, int LR0, int LR1, int LR2, int G_, int SBX_ = 0, int MINB_ = 1,
+          bool DIT = false>
 struct RowCfg {
-    using S = Steps<LOGN, LOGE, LR0, LR1, LR2>;
+    using S = Steps<LOGN, LOGE, LR0, LR1, LR2, DIT>;
     static constexpr int G = G_;
     static constexpr int THREADS = S::T * G;
     static constexpr int MINB = MINB_;

@@ -26,6 +26,7 @@ struct LaunchArgs {
     W64 w64;                // register-DFT constants
     float2* scratch;        // per-CTA scratch (kernels that need it), else null
     int* status;            // device status word
+    const void* aux;        // kernel-specific constant data (split path: block matrices)
     int grid;               // CTAs to launch
     cudaStream_t stream;
     bool adj;

@@ -134,6 +134,7 @@ extern "C" int sdft_execute_noalloc(int64_t n, int64_t batch, int direction, con
     a.w64 = state.w64;
     a.scratch = state.scratch;
     a.status = nullptr;
+    a.aux = nullptr;
     a.grid = (int)(batch < slots ? batch : slots);
     a.stream = (cudaStream_t)stream;
     a.adj = (direction == SDFT_ADJOINT);

@@ -1,13 +1,18 @@
-// rows_1024.cu -- compiled row-kernel configuration for N = 1024: one warp
-// per transform, radix [32, 32] (32 complex values per lane), one padded
-// shared-memory exchange between the two register steps.
+// rows_1024.cu -- compiled row-kernel candidates for N = 1024.  Candidate 0:
+// one warp per transform, radix [32, 32] (32 complex values per lane), one
+// padded shared-memory exchange between the two register steps.
 #include "kernels_rows.cuh"
 
 namespace sdft {
 
-const KernelInfo* rows_kernel_1024(int logn) {
-    static const KernelInfo k10 = rows_info<RowCfg<10, 5, 5, 5, 0, 8, 0, 2>>("N=1024: 32 threads/transform, radix [32,32]");
-    return logn == 10 ? &k10 : nullptr;
+const KernelInfo* rows_candidate_1024(int logn, int idx) {
+    static const KernelInfo k10[] = {
+        rows_info<RowCfg<10, 5, 5, 5, 0, 8, 0, 2>>("N=1024: 32 threads/transform, radix [32,32]"),
+        rows_info<RowCfg<10, 5, 5, 5, 0, 8, 0, 2, true>>("N=1024: 32 threads/transform, radix [32,32], Eq. (6) order"),
+        rows_info<RowCfg<10, 5, 5, 5, 0, 4, 0, 4>>("N=1024: 32 threads/transform, radix [32,32], 128-thread CTAs"),
+        rows_info<RowCfg<10, 4, 4, 3, 3, 4, 0, 4>>("N=1024: 64 threads/transform, radix [16,8,8]")};
+    if (logn != 10 || idx < 0 || idx >= (int)(sizeof(k10) / sizeof(k10[0]))) return nullptr;
+    return &k10[idx];
 }
 
 }  // namespace sdft

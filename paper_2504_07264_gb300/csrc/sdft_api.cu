@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <set>
@@ -18,18 +19,23 @@
 #include "../../include/sdft.h"
 #include "launch.h"
 #include "ragged.h"
+#include "split.h"
 
 namespace sdft {
-const KernelInfo* rows_kernel_small(int logn);
-const KernelInfo* rows_kernel_1024(int logn);
-const KernelInfo* rows_kernel_big(int logn);
+const KernelInfo* rows_candidate_small(int logn, int idx);
+const KernelInfo* rows_candidate_1024(int logn, int idx);
+const KernelInfo* rows_candidate_big(int logn, int idx);
 
-const KernelInfo* rows_kernel(int logn) {
-    if (logn >= 1 && logn <= 9) return rows_kernel_small(logn);
-    if (logn == 10) return rows_kernel_1024(logn);
-    if (logn >= 11 && logn <= 14) return rows_kernel_big(logn);
+// Compiled FP32 schedule `idx` for log2 N (null past the last one).
+const KernelInfo* f32_candidate(int logn, int idx) {
+    if (logn >= 1 && logn <= 9) return rows_candidate_small(logn, idx);
+    if (logn == 10) return rows_candidate_1024(logn, idx);
+    if (logn >= 11 && logn <= 14) return rows_candidate_big(logn, idx);
+    if (logn >= 15 && logn <= 16) return idx == 0 ? large_kernel(logn) : nullptr;
     return nullptr;
 }
+
+const KernelInfo* rows_kernel(int logn) { return f32_candidate(logn, 0); }
 }  // namespace sdft
 
 using namespace sdft;
@@ -47,6 +53,7 @@ int fail(int status) {
 }
 
 struct HostStaging {
+    int mode = 0;                      // SDFT_HOST_AUTO / _STAGED / _ZERO_COPY
     int64_t chunk = 0;                 // transforms per chunk
     float* d_buf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [slot][plane]
     cudaStream_t streams[2] = {nullptr, nullptr};
@@ -86,6 +93,7 @@ struct sdft_plan {
     float2* d_tw;
     float2* d_scratch;
     int* d_status;
+    void* d_aux;          // split path: block-matrix images
     W64 w64;
     HostStaging host;
     RaggedState rag;
@@ -95,6 +103,24 @@ namespace {
 
 std::mutex g_registry_mu;
 std::set<const sdft_plan*> g_registry;
+
+// process-wide schedule choice per log2 N for the FP32 path (autotuner)
+std::atomic<int> g_choice[17];
+
+int candidate_count(int logn, int dtype) {
+    if (dtype != SDFT_F32) return split_kernel(logn, dtype) ? 1 : 0;
+    int c = 0;
+    while (f32_candidate(logn, c)) ++c;
+    return c;
+}
+
+const KernelInfo* candidate(int logn, int dtype, int idx) {
+    if (dtype != SDFT_F32) {
+        const SplitInfo* si = split_kernel(logn, dtype);
+        return (si && idx == 0) ? &si->kern : nullptr;
+    }
+    return f32_candidate(logn, idx);
+}
 
 bool plan_alive(const sdft_plan* p) {
     if (p == nullptr) return false;
@@ -113,6 +139,7 @@ void free_plan_memory(sdft_plan* p) {
     if (p->d_tw) cudaFree(p->d_tw);
     if (p->d_scratch) cudaFree(p->d_scratch);
     if (p->d_status) cudaFree(p->d_status);
+    if (p->d_aux) cudaFree(p->d_aux);
     for (int s = 0; s < 2; ++s) {
         for (int pl = 0; pl < 2; ++pl)
             if (p->host.d_buf[s][pl]) cudaFree(p->host.d_buf[s][pl]);
@@ -175,6 +202,7 @@ int launch(const sdft_plan* p, int direction, const float* xr, const float* xi, 
     a.w64 = p->w64;
     a.scratch = scratch;
     a.status = p->d_status;
+    a.aux = p->d_aux;
     a.grid = p->grid;
     a.stream = stream;
     a.adj = (direction == SDFT_ADJOINT);
@@ -237,6 +265,17 @@ int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi,
     return cudaGraphLaunch(r.exec[d], stream) == cudaSuccess ? SDFT_OK : SDFT_ERR_CUDA;
 }
 
+// Device-side address of page-locked host memory the GPU can reach directly
+// (null if `p` is not such memory).
+const void* mapped_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error this query leaves for plain host memory
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
+}
+
 int run(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr, float* yi,
         cudaStream_t stream, long long batch, float2* scratch) {
     if (p->rag.on) return launch_ragged(p, direction, xr, xi, yr, yi, stream, scratch);
@@ -267,14 +306,34 @@ const char* sdft_status_string(int status) {
     }
 }
 
+sdft_plan* plan_create_idx(int64_t n, int64_t batch, int dtype, int idx);
+
 sdft_plan* sdft_plan_create(int64_t n, int64_t batch, int dtype) {
+    const int logn = log2_exact(n);
+    const int idx = (logn >= 1 && logn <= kMaxLogN && dtype == SDFT_F32) ? g_choice[logn].load() : 0;
+    return plan_create_idx(n, batch, dtype, idx);
+}
+
+sdft_plan* plan_create_idx(int64_t n, int64_t batch, int dtype, int idx) {
     const int logn = log2_exact(n);
     if (logn < 1 || logn > kMaxLogN) { fail(SDFT_ERR_UNSUPPORTED_N); return nullptr; }
     if (batch < 1) { fail(SDFT_ERR_INVALID_ARG); return nullptr; }
-    if (dtype != SDFT_F32) { fail(SDFT_ERR_UNSUPPORTED_DTYPE); return nullptr; }
+    if (dtype != SDFT_F32 && dtype != SDFT_F32_SPLIT_BF16 && dtype != SDFT_F32_SPLIT_FP16) {
+        fail(SDFT_ERR_UNSUPPORTED_DTYPE);
+        return nullptr;
+    }
     if (batch > ((int64_t)1 << 40) / n) { fail(SDFT_ERR_INVALID_ARG); return nullptr; }
 
-    const KernelInfo* k = logn <= 14 ? rows_kernel(logn) : large_kernel(logn);
+    const SplitInfo* si = nullptr;
+    const KernelInfo* k = nullptr;
+    if (dtype == SDFT_F32) {
+        k = f32_candidate(logn, idx);
+        if (!k) k = f32_candidate(logn, 0);
+    } else {
+        si = split_kernel(logn, dtype);   // tensor-core path: N = 256 and 1024
+        if (!si) { fail(SDFT_ERR_UNSUPPORTED_DTYPE); return nullptr; }
+        k = &si->kern;
+    }
     if (!k) { fail(SDFT_ERR_UNSUPPORTED_N); return nullptr; }
 
     sdft_plan* p = new (std::nothrow) sdft_plan();
@@ -312,6 +371,10 @@ sdft_plan* sdft_plan_create(int64_t n, int64_t batch, int dtype) {
         // the register constants first (uses the table memory as scratch)
         if (make_w64(&p->w64, p->d_tw, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
         if (make_tables(p->d_tw, k->tables, k->ntables, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        if (si) {
+            if (cudaMalloc(&p->d_aux, si->aux_bytes) != cudaSuccess) { status = SDFT_ERR_ALLOC; break; }
+            if (si->make_aux(p->d_aux, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        }
         if (cudaStreamSynchronize(st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
     } while (0);
     if (st) cudaStreamDestroy(st);
@@ -491,6 +554,23 @@ int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const flo
     HostStaging& h = plan->host;
     const int64_t n = plan->n;
     const bool rag = plan->rag.on;
+    if (h.mode != SDFT_HOST_STAGED) {
+        // zero copy: the kernel reads and writes the page-locked host buffers
+        // directly over the CPU-GPU link (no staging, no copy engines)
+        const float* dxr = static_cast<const float*>(mapped_host(xr));
+        const float* dxi = static_cast<const float*>(mapped_host(xi));
+        float* dyr = static_cast<float*>(const_cast<void*>(mapped_host(yr)));
+        float* dyi = static_cast<float*>(const_cast<void*>(mapped_host(yi)));
+        if (dxr && dxi && dyr && dyi) {
+            s = check_buffers(plan, dxr, dxi, dyr, dyi);
+            if (s != SDFT_OK) return fail(s);
+            cudaStream_t user = (cudaStream_t)stream;
+            s = run(plan, direction, dxr, dxi, dyr, dyi, user, plan->batch, plan->d_scratch);
+            if (s != SDFT_OK) return fail(s);
+            return cudaStreamSynchronize(user) == cudaSuccess ? SDFT_OK : fail(SDFT_ERR_CUDA);
+        }
+        if (h.mode == SDFT_HOST_ZERO_COPY) return fail(SDFT_ERR_INVALID_ARG);
+    }
     if (h.chunk == 0) {
         // ~32 MiB per plane per slot, whole transforms, at least one; a ragged
         // plan moves its whole batch as one chunk
@@ -543,6 +623,14 @@ int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const flo
     return SDFT_OK;
 }
 
+int sdft_plan_set_host_mode(sdft_plan* plan, int mode) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    if (mode != SDFT_HOST_AUTO && mode != SDFT_HOST_STAGED && mode != SDFT_HOST_ZERO_COPY)
+        return fail(SDFT_ERR_INVALID_ARG);
+    plan->host.mode = mode;
+    return SDFT_OK;
+}
+
 int sdft_plan_sync_status(const sdft_plan* plan, void* stream) {
     if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
     int s = check_device(plan);
@@ -586,6 +674,81 @@ int sdft_plan_describe(const sdft_plan* plan, char* buf, int64_t len) {
                          "%s; %d threads/CTA, %zu B smem, grid %d, %d transform(s)/CTA tile",
                          plan->kern->name, plan->kern->threads, plan->kern->smem, plan->grid,
                          plan->kern->transforms_per_cta);
+}
+
+int sdft_schedule_count(int64_t n, int dtype) {
+    const int logn = log2_exact(n);
+    if (logn < 1 || logn > kMaxLogN) return -fail(SDFT_ERR_UNSUPPORTED_N);
+    const int c = candidate_count(logn, dtype);
+    return c > 0 ? c : -fail(SDFT_ERR_UNSUPPORTED_DTYPE);
+}
+
+int sdft_schedule_describe(int64_t n, int dtype, int index, char* buf, int64_t len) {
+    const int logn = log2_exact(n);
+    if (logn < 1 || logn > kMaxLogN) return -fail(SDFT_ERR_UNSUPPORTED_N);
+    const KernelInfo* k = candidate(logn, dtype, index);
+    if (!k) return -fail(SDFT_ERR_INVALID_ARG);
+    return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
+                         "%s; %d threads/CTA, %zu B smem, %d transform(s)/CTA tile", k->name,
+                         k->threads, k->smem, k->transforms_per_cta);
+}
+
+int sdft_schedule_select(int64_t n, int dtype, int index) {
+    const int logn = log2_exact(n);
+    if (logn < 1 || logn > kMaxLogN) return fail(SDFT_ERR_UNSUPPORTED_N);
+    if (!candidate(logn, dtype, index)) return fail(SDFT_ERR_INVALID_ARG);
+    if (dtype == SDFT_F32) g_choice[logn].store(index);
+    return SDFT_OK;
+}
+
+int sdft_schedule_selected(int64_t n, int dtype) {
+    const int logn = log2_exact(n);
+    if (logn < 1 || logn > kMaxLogN) return -fail(SDFT_ERR_UNSUPPORTED_N);
+    if (candidate_count(logn, dtype) == 0) return -fail(SDFT_ERR_UNSUPPORTED_DTYPE);
+    return dtype == SDFT_F32 ? g_choice[logn].load() : 0;
+}
+
+int sdft_autotune(int64_t n, int64_t batch, int dtype, const float* xr, const float* xi, float* yr,
+                  float* yi, int reps, float* ms_out, void* stream) {
+    const int logn = log2_exact(n);
+    if (logn < 1 || logn > kMaxLogN) return -fail(SDFT_ERR_UNSUPPORTED_N);
+    if (batch < 1 || reps < 1) return -fail(SDFT_ERR_INVALID_ARG);
+    const int count = candidate_count(logn, dtype);
+    if (count == 0) return -fail(SDFT_ERR_UNSUPPORTED_DTYPE);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return -fail(SDFT_ERR_CUDA);
+    }
+    int best = -1;
+    float best_ms = 0.f;
+    int status = SDFT_OK;
+    for (int idx = 0; idx < count && status == SDFT_OK; ++idx) {
+        sdft_plan* p = plan_create_idx(n, batch, dtype, idx);
+        if (!p) { status = g_last_error; break; }
+        float ms = 0.f;
+        int s = check_buffers(p, xr, xi, yr, yi);
+        for (int w = 0; w < 2 && s == SDFT_OK; ++w)
+            s = launch(p, SDFT_FORWARD, xr, xi, yr, yi, st, batch, p->d_scratch);
+        if (s == SDFT_OK && cudaEventRecord(e0, st) != cudaSuccess) s = SDFT_ERR_CUDA;
+        for (int r = 0; r < reps && s == SDFT_OK; ++r)
+            s = launch(p, SDFT_FORWARD, xr, xi, yr, yi, st, batch, p->d_scratch);
+        if (s == SDFT_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            s = SDFT_ERR_CUDA;
+        sdft_plan_destroy(p);
+        if (s != SDFT_OK) { status = s; break; }
+        ms /= (float)reps;
+        if (ms_out) ms_out[idx] = ms;
+        if (best < 0 || ms < best_ms) { best = idx; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != SDFT_OK) return -fail(status);
+    if (dtype == SDFT_F32) g_choice[logn].store(best);
+    return best;
 }
 
 }  // extern "C"

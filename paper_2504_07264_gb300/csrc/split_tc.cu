@@ -1,0 +1,359 @@
+// split_tc.cu -- split-precision tensor-core path (SDFT_F32_SPLIT_BF16 and
+// SDFT_F32_SPLIT_FP16) for N = 256 and N = 1024.
+//
+// N = R * R.  A radix-R block of the DFT is a dense real contraction: on the
+// stacked planes of R inputs, the R-point DFT is the 2R x 2R real matrix of
+// Eqs. (4)-(5), [y^r; y^i] = [C S; -S C] [x^r; x^i] (its transpose for the
+// adjoint).  The transform is two such blocks (the regrouping of Eq. (6) into
+// radix-R steps used everywhere in this library):
+//   GEMM 1: rows (transform b, column c), K = [x^r, x^i](c + R * ntop), ntop < R
+//           -> D1[(b, c)][(re/im, d)]                       (tcgen05, TMEM)
+//   rotate D1 by W_N^{c * d} in float32
+//   GEMM 2: rows (b, d), K = the rotated values over c      (tcgen05, TMEM)
+//           -> y[b][d + R * k2]
+// Each GEMM runs on 16-bit operands with float32 accumulation: every operand
+// is split into hi + lo 16-bit parts (x = hi + lo + O(2^-16 |x|) for bf16) and
+// the product is accumulated as hi*B_lo + lo*B_hi + hi*B_hi (the lo*lo term is
+// dropped).  Before each split the transform is scaled by a power of two so
+// that its largest magnitude lies in [0.5, 1) (keeps FP16 in range and its lo
+// parts normal); the scales are undone exactly at the end.
+//
+// One CTA of 128 threads (a warpgroup) owns 128 GEMM rows = 128 / R
+// transforms per tile; thread i owns row i and TMEM lane i.  Thread 0 issues
+// the MMAs (6 per GEMM for R = 16, 12 for R = 32) and commits them to an
+// mbarrier; the block matrices (hi and lo) arrive once per CTA by a 1-D bulk
+// copy (TMA).  Operands are K-major, no swizzle: 8-row x 16-byte core
+// matrices, K-adjacent core matrices 128 B apart, 8-row groups K/8*128 B apart.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "../../include/sdft.h"
+#include "fft_core.cuh"
+#include "launch.h"
+#include "split.h"
+#include "tc_ptx.cuh"
+#include "twiddle.cuh"
+
+namespace sdft {
+namespace {
+
+template <int LOGR, bool FP16>
+struct SplitCfg {
+    static constexpr int R = 1 << LOGR, N = R * R, LOGN = 2 * LOGR;
+    static constexpr int ROWS = 128;            // MMA M
+    static constexpr int TPT = ROWS / R;        // transforms per tile
+    static constexpr int K = 2 * R;             // [re(0..R-1), im(0..R-1)]
+    static constexpr int NM = 2 * R;            // MMA N
+    static constexpr int SBO = (K / 8) * 128;   // bytes between 8-row groups
+    static constexpr int LBO = 128;             // bytes between K-adjacent core matrices
+    static constexpr int A_BYTES = ROWS * K * 2;
+    static constexpr int B_BYTES = NM * K * 2;
+    static constexpr int TMEM_COLS = 2 * NM;    // D1 and D2 (64 or 128 columns)
+    static constexpr int MAX_CTAS = 512 / TMEM_COLS;
+    static constexpr int MINB = MAX_CTAS > 4 ? 4 : MAX_CTAS;
+    static constexpr uint32_t IDESC = tc::idesc_f16(FP16, ROWS, NM);
+    // A hi, A lo, B hi, B lo, plus alignment slack; raised so that no more
+    // CTAs fit on an SM (228 KiB) than its 512 TMEM columns can serve.
+    static constexpr size_t NEED = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 1024;
+    static constexpr size_t FLOOR = (size_t)(228 * 1024) / (MAX_CTAS + 1) + 1024;
+    static constexpr size_t SMEM = NEED > FLOOR ? NEED : FLOOR;
+    static_assert(R == 16 || R == 32, "split path covers N = 256 and 1024");
+};
+
+// byte offset of element (row, k) in a K-major, no-swizzle operand
+__host__ __device__ constexpr uint32_t kmaj(int row, int k, int sbo) {
+    return (uint32_t)((row & 7) * 16 + (row >> 3) * sbo + (k & 7) * 2 + (k >> 3) * 128);
+}
+
+template <bool FP16>
+__device__ __forceinline__ void split16(const float v, uint16_t& hi, uint16_t& lo) {
+    if constexpr (FP16) {
+        const __half h = __float2half_rn(v);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+    }
+}
+
+// D (TMEM columns at dt) = A * B over the three split terms, small terms first.
+template <class CFG>
+__device__ __forceinline__ void issue_gemm(uint32_t dt, uint32_t a_hi, uint32_t a_lo,
+                                           uint32_t b_hi, uint32_t b_lo) {
+    const uint32_t as[3] = {a_hi, a_lo, a_hi};
+    const uint32_t bs[3] = {b_lo, b_hi, b_hi};
+#pragma unroll
+    for (int term = 0; term < 3; ++term)
+#pragma unroll
+        for (int kk = 0; kk < CFG::K / 16; ++kk) {
+            const uint64_t ad = tc::smem_desc(as[term] + kk * 256, CFG::LBO, CFG::SBO);
+            const uint64_t bd = tc::smem_desc(bs[term] + kk * 256, CFG::LBO, CFG::SBO);
+            tc::mma_f16(dt, ad, bd, CFG::IDESC, (term | kk) != 0);
+        }
+}
+
+// 2R consecutive TMEM columns of this thread's lane
+template <int R>
+__device__ __forceinline__ void tmem_row(uint32_t taddr, float (&v)[2 * R]) {
+    if constexpr (R == 16) {
+        tc::tmem_ld32(taddr, v);
+    } else {
+        float a[32], b[32];
+        tc::tmem_ld32(taddr, a);
+        tc::tmem_ld32(taddr + 32, b);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) { v[i] = a[i]; v[32 + i] = b[i]; }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ int block_exponent(const float (&v)[2 * R]) {
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) m = fmaxf(m, fabsf(v[i]));
+#pragma unroll
+    for (int o = 1; o < R; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e = 0;
+    frexpf(m, &e);      // m = f * 2^e, f in [0.5, 1); 0 for m = 0
+    return e;
+}
+
+template <class CFG, bool ADJ>
+__global__ void __launch_bounds__(128, CFG::MINB)
+k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
+        const uint16_t* __restrict__ bimg, const float2* __restrict__ tw, int* status) {
+    constexpr int R = CFG::R, N = CFG::N, NM = CFG::NM, TPT = CFG::TPT;
+    extern __shared__ uint8_t smraw[];
+    uint8_t* const sm = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t* const a_hi = sm;
+    uint8_t* const a_lo = sm + CFG::A_BYTES;
+    uint8_t* const b_hi = sm + 2 * CFG::A_BYTES;
+    uint8_t* const b_lo = b_hi + CFG::B_BYTES;
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = (int)threadIdx.x;
+    const int warp = tid >> 5;
+    const uint32_t mb0 = tc::smem_u32(&mbar[0]);
+    const uint32_t mb1 = tc::smem_u32(&mbar[1]);
+    const uint32_t sa_hi = tc::smem_u32(a_hi), sa_lo = tc::smem_u32(a_lo);
+    const uint32_t sb_hi = tc::smem_u32(b_hi), sb_lo = tc::smem_u32(b_lo);
+
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_base), CFG::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(mb0, 1);
+        tc::mbar_init(mb1, 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+
+    // the block matrices (hi then lo) of this direction, once per CTA
+    if (tid == 0) {
+        tc::mbar_expect_tx(mb1, 2 * CFG::B_BYTES);
+        tc::bulk_g2s(sb_hi, bimg + (ADJ ? CFG::B_BYTES : 0), 2 * CFG::B_BYTES, mb1);
+    }
+    int bad = __syncthreads_or(!tc::mbar_wait(mb1, 0));
+    uint32_t phase = 0;
+
+    const long long ntiles = (batch + TPT - 1) / TPT;
+    const int bl = tid / R;          // transform within the tile
+    const int c = tid % R;           // column (step 1) / output digit d (step 2)
+    for (long long tile = blockIdx.x; !bad && tile < ntiles; tile += gridDim.x) {
+        const long long b = tile * TPT + bl;
+        const bool active = b < batch;
+        const long long base = (active ? b : 0) * (long long)N;
+        // ---- GEMM 1 operand: x[c + R * ntop], scaled and split
+        float v[2 * R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            v[t] = active ? xr[base + c + R * t] : 0.f;
+            v[R + t] = active ? xi[base + c + R * t] : 0.f;
+        }
+        const int e0 = block_exponent<R>(v);
+        const float s0 = ldexpf(1.f, -e0);
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) {
+            uint16_t h, l;
+            split16<CFG::FP16_>(v[k] * s0, h, l);
+            const uint32_t o = kmaj(tid, k, CFG::SBO);
+            *reinterpret_cast<uint16_t*>(a_hi + o) = h;
+            *reinterpret_cast<uint16_t*>(a_lo + o) = l;
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue_gemm<CFG>(tbase, sa_hi, sa_lo, sb_hi, sb_lo);
+            tc::mma_commit(mb0);
+        }
+        if (__syncthreads_or(!tc::mbar_wait(mb0, phase))) { bad = 1; break; }
+        phase ^= 1;
+        tc::fence_after_sync();
+        // ---- rotate row (b, c) by W_N^{c d}, rescale, split into GEMM 2 rows (b, d)
+        float d1[2 * R];
+        tmem_row<R>(lane_base, d1);
+#pragma unroll
+        for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], __ldg(tw + d * R + c));
+        const int e1 = block_exponent<R>(d1);
+        const float s1 = ldexpf(1.f, -e1);
+#pragma unroll
+        for (int d = 0; d < R; ++d) {
+            uint16_t h, l;
+            const int row = bl * R + d;
+            split16<CFG::FP16_>(d1[d] * s1, h, l);
+            const uint32_t o = kmaj(row, c, CFG::SBO);
+            *reinterpret_cast<uint16_t*>(a_hi + o) = h;
+            *reinterpret_cast<uint16_t*>(a_lo + o) = l;
+            split16<CFG::FP16_>(d1[R + d] * s1, h, l);
+            const uint32_t o2 = kmaj(row, R + c, CFG::SBO);
+            *reinterpret_cast<uint16_t*>(a_hi + o2) = h;
+            *reinterpret_cast<uint16_t*>(a_lo + o2) = l;
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue_gemm<CFG>(tbase + NM, sa_hi, sa_lo, sb_hi, sb_lo);
+            tc::mma_commit(mb0);
+        }
+        if (__syncthreads_or(!tc::mbar_wait(mb0, phase))) { bad = 1; break; }
+        phase ^= 1;
+        tc::fence_after_sync();
+        // ---- row (b, d): y[d + R * k2] for every k2, scales undone
+        float d2[2 * R];
+        tmem_row<R>(lane_base + NM, d2);
+        tc::fence_before_sync();
+        const float us = ldexpf(1.f, e0 + e1);
+        if (active) {
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) {
+                yr[base + c + R * k2] = d2[k2] * us;
+                yi[base + c + R * k2] = d2[R + k2] * us;
+            }
+        }
+    }
+    if (bad && tid == 0) atomicExch(status, SDFT_ERR_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, CFG::TMEM_COLS);
+    }
+}
+
+template <int LOGR, bool FP16>
+struct SplitCfgT : SplitCfg<LOGR, FP16> {
+    static constexpr bool FP16_ = FP16;
+};
+
+// Block-matrix images, forward then adjoint, each hi then lo, laid out exactly
+// as the kernel's shared-memory B operand: row n = output (re d | im d),
+// column k = input (re t | im t).
+template <class CFG>
+__global__ void k_bimg(uint16_t* dst) {
+    constexpr int R = CFG::R;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= 2 * CFG::NM * CFG::K) return;
+    const bool adj = u >= CFG::NM * CFG::K;
+    const int nk = u % (CFG::NM * CFG::K);
+    const int n = nk / CFG::K, k = nk % CFG::K;
+    const int d = n % R, t = k % R;
+    const float2 w = twiddle_value((int64_t)((d * t) % R), R);   // (cos, -sin) of 2 pi d t / R
+    const float cs = w.x, sn = adj ? w.y : -w.y;                  // sin for the forward
+    float coef;
+    if (n < R) coef = (k < R) ? cs : sn;     // y^r = C x^r + S x^i
+    else coef = (k < R) ? -sn : cs;          // y^i = -S x^r + C x^i
+    uint16_t h, l;
+    split16<CFG::FP16_>(coef, h, l);
+    const uint32_t o = kmaj(n, k, CFG::SBO) / 2;
+    uint16_t* img = dst + (adj ? 2 * CFG::B_BYTES / 2 : 0);
+    img[o] = h;
+    img[CFG::B_BYTES / 2 + o] = l;
+}
+
+template <class CFG>
+cudaError_t split_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_split<CFG, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CFG::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_split<CFG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)CFG::SMEM);
+}
+
+template <class CFG>
+int split_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_split<CFG, false>, 128, CFG::SMEM) !=
+        cudaSuccess)
+        return 0;
+    return n < CFG::MAX_CTAS ? n : CFG::MAX_CTAS;
+}
+
+template <class CFG>
+cudaError_t split_launch(const LaunchArgs& a) {
+    const uint16_t* bimg = static_cast<const uint16_t*>(a.aux);
+    if (a.adj)
+        return launch_kernel(k_split<CFG, true>, a.grid, 128, CFG::SMEM, a.stream, a.xr, a.xi, a.yr,
+                             a.yi, a.batch, bimg, a.tw, a.status);
+    return launch_kernel(k_split<CFG, false>, a.grid, 128, CFG::SMEM, a.stream, a.xr, a.xi, a.yr,
+                         a.yi, a.batch, bimg, a.tw, a.status);
+}
+
+template <class CFG>
+cudaError_t split_make_aux(void* dst, cudaStream_t stream) {
+    const int total = 2 * CFG::NM * CFG::K;
+    return launch_kernel(k_bimg<CFG>, (total + 255) / 256, 256, 0, stream,
+                         static_cast<uint16_t*>(dst));
+}
+
+template <class CFG>
+SplitInfo split_info(const char* name) {
+    SplitInfo s = {};
+    KernelInfo& k = s.kern;
+    k.name = name;
+    k.logn = CFG::LOGN;
+    k.threads = 128;
+    k.smem = CFG::SMEM;
+    k.transforms_per_cta = CFG::TPT;
+    k.ntables = 1;
+    k.tables[0] = TableDesc{CFG::N, CFG::R, CFG::R, 0};   // W_N^{c d} at [d][c]
+    k.tw_entries = CFG::N;
+    k.scratch_per_cta = 0;
+    k.launches = 1;
+    k.prepare = split_prepare<CFG>;
+    k.blocks_per_sm = split_blocks_per_sm<CFG>;
+    k.launch = split_launch<CFG>;
+    s.aux_bytes = 4 * (size_t)CFG::B_BYTES;
+    s.make_aux = split_make_aux<CFG>;
+    return s;
+}
+
+}  // namespace
+
+const SplitInfo* split_kernel(int logn, int dtype) {
+    static const SplitInfo b8 = split_info<SplitCfgT<4, false>>(
+        "N=256 split-BF16 tensor cores: two 128x32x32 tcgen05 GEMMs (3 terms each) per 8 transforms");
+    static const SplitInfo h8 = split_info<SplitCfgT<4, true>>(
+        "N=256 split-FP16 tensor cores: two 128x32x32 tcgen05 GEMMs (3 terms each) per 8 transforms");
+    static const SplitInfo b10 = split_info<SplitCfgT<5, false>>(
+        "N=1024 split-BF16 tensor cores: two 128x64x64 tcgen05 GEMMs (3 terms each) per 4 transforms");
+    static const SplitInfo h10 = split_info<SplitCfgT<5, true>>(
+        "N=1024 split-FP16 tensor cores: two 128x64x64 tcgen05 GEMMs (3 terms each) per 4 transforms");
+    const bool fp16 = dtype == SDFT_F32_SPLIT_FP16;
+    if (logn == 8) return fp16 ? &h8 : &b8;
+    if (logn == 10) return fp16 ? &h10 : &b10;
+    return nullptr;
+}
+
+}  // namespace sdft

@@ -37,6 +37,9 @@ SDFT_F32_SPLIT_BF16 = 1
 SDFT_F32_SPLIT_FP16 = 2
 SDFT_FORWARD = 0
 SDFT_ADJOINT = 1
+SDFT_HOST_AUTO = 0
+SDFT_HOST_STAGED = 1
+SDFT_HOST_ZERO_COPY = 2
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -49,7 +52,13 @@ _SIGS = {
     "sdft_execute": ([_P, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
     "sdft_execute_host": ([_P, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
     "sdft_plan_sync_status": ([_P, _P], ctypes.c_int),
+    "sdft_plan_set_host_mode": ([_P, ctypes.c_int], ctypes.c_int),
     "sdft_execute_noalloc": ([_I64, _I64, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
+    "sdft_schedule_count": ([_I64, ctypes.c_int], ctypes.c_int),
+    "sdft_schedule_describe": ([_I64, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, _I64], ctypes.c_int),
+    "sdft_schedule_select": ([_I64, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sdft_schedule_selected": ([_I64, ctypes.c_int], ctypes.c_int),
+    "sdft_autotune": ([_I64, _I64, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, _P, _P], ctypes.c_int),
     "sdft_plan_n": ([_P], _I64),
     "sdft_plan_batch": ([_P], _I64),
     "sdft_plan_points": ([_P], _I64),
@@ -130,6 +139,35 @@ def sdft_execute_noalloc(n, batch, direction, xr, xi, yr, yi, stream) -> int:
     return lib().sdft_execute_noalloc(n, batch, direction, xr, xi, yr, yi, stream)
 
 
+def sdft_schedule_count(n: int, dtype: int = SDFT_F32) -> int:
+    return lib().sdft_schedule_count(n, dtype)
+
+
+def sdft_schedule_describe(n: int, dtype: int, index: int) -> str:
+    need = lib().sdft_schedule_describe(n, dtype, index, None, 0)
+    if need < 0:
+        raise SdftError(-need, "sdft_schedule_describe")
+    buf = ctypes.create_string_buffer(need + 1)
+    lib().sdft_schedule_describe(n, dtype, index, buf, need + 1)
+    return buf.value.decode()
+
+
+def sdft_schedule_select(n: int, dtype: int, index: int) -> int:
+    return lib().sdft_schedule_select(n, dtype, index)
+
+
+def sdft_schedule_selected(n: int, dtype: int = SDFT_F32) -> int:
+    return lib().sdft_schedule_selected(n, dtype)
+
+
+def sdft_autotune(n, batch, dtype, xr, xi, yr, yi, reps, ms_out, stream) -> int:
+    return lib().sdft_autotune(n, batch, dtype, xr, xi, yr, yi, reps, ms_out, stream)
+
+
+def sdft_plan_set_host_mode(plan, mode: int) -> int:
+    return lib().sdft_plan_set_host_mode(plan, mode)
+
+
 def sdft_plan_sync_status(plan, stream) -> int:
     return lib().sdft_plan_sync_status(plan, stream)
 
@@ -202,6 +240,8 @@ class Plan:
     def __init__(self, n: int | None = None, batch: int | None = None, dtype: int = SDFT_F32,
                  lengths=None):
         self._h = 0
+        from . import autotune
+        autotune.ensure_applied()
         if lengths is not None:
             import numpy as np
             arr = np.ascontiguousarray(lengths, dtype=np.int64)
@@ -291,6 +331,9 @@ class Plan:
                 ptrs.append(a.ctypes.data)
         st = sdft_execute_host(self.handle, direction, *ptrs, _stream_handle(stream))
         _check(st, "sdft_execute_host")
+
+    def set_host_mode(self, mode: int) -> None:
+        _check(sdft_plan_set_host_mode(self.handle, mode), "sdft_plan_set_host_mode")
 
     def sync_status(self, stream=None) -> int:
         return sdft_plan_sync_status(self.handle, _stream_handle(stream))

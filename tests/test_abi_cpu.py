@@ -65,6 +65,11 @@ def test_bad_batch_rejected(batch):
 def test_bad_dtype_rejected():
     assert S.sdft_plan_create(1024, 4, 7) == 0
     assert S.sdft_last_error() == S.SDFT_ERR_UNSUPPORTED_DTYPE
+    # the split tensor-core path exists for N = 256 and 1024 only
+    for n in (16, 512, 2048):
+        for dt in (S.SDFT_F32_SPLIT_BF16, S.SDFT_F32_SPLIT_FP16):
+            assert S.sdft_plan_create(n, 4, dt) == 0
+            assert S.sdft_last_error() == S.SDFT_ERR_UNSUPPORTED_DTYPE
 
 
 @pytest.mark.parametrize("handle", [0, 12345678, 0xDEADBEEF0])

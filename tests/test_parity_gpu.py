@@ -144,6 +144,7 @@ def test_host_buffers_match_device_path(logn):
     import torch
 
     from paper_2504_07264_gb300 import Plan
+    from paper_2504_07264_gb300 import sdft as S
     n = 1 << logn
     batch = max(2, (1 << 21) // n) + 1
     xr, xi = W.normal_planes(n, batch, seed=600 + logn)
@@ -151,10 +152,15 @@ def test_host_buffers_match_device_path(logn):
         dev = gpu_run(xr, xi, 0, plan=plan)
         hxr = torch.from_numpy(xr).pin_memory()
         hxi = torch.from_numpy(xi).pin_memory()
-        hyr = torch.empty_like(hxr).pin_memory()
-        hyi = torch.empty_like(hxi).pin_memory()
-        plan.execute_host(0, hxr, hxi, hyr, hyi)
-    assert np.array_equal(dev[0], hyr.numpy()) and np.array_equal(dev[1], hyi.numpy())
+        for mode in (S.SDFT_HOST_AUTO, S.SDFT_HOST_STAGED, S.SDFT_HOST_ZERO_COPY):
+            hyr = torch.full_like(hxr, float("nan")).pin_memory()
+            hyi = torch.full_like(hxi, float("nan")).pin_memory()
+            plan.set_host_mode(mode)
+            plan.execute_host(0, hxr, hxi, hyr, hyi)
+            assert np.array_equal(dev[0], hyr.numpy()) and np.array_equal(dev[1], hyi.numpy()), mode
+        # zero copy needs page-locked buffers; pageable ones are refused
+        with pytest.raises(S.SdftError):
+            plan.execute_host(0, xr, xi, np.empty_like(xr), np.empty_like(xi))
 
 
 def test_argument_errors_on_device():

@@ -1,0 +1,63 @@
+"""Every compiled schedule of every length matches the oracle (GPU), and the
+autotuner picks one of them."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import TOL_F32, gpu_run, rel_l2_rows
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2504_07264_gb300 import build
+    build.build()
+    O.build()
+
+
+def _cases():
+    from paper_2504_07264_gb300 import build
+    from paper_2504_07264_gb300 import sdft as S
+    build.build()
+    out = []
+    for m in range(1, 17):
+        for i in range(1, max(1, S.sdft_schedule_count(1 << m, 0))):
+            out.append((m, i))
+    return out
+
+
+@pytest.mark.parametrize("logn,idx", _cases())
+def test_schedule_matches_oracle(logn, idx):
+    from paper_2504_07264_gb300 import Plan
+    from paper_2504_07264_gb300 import sdft as S
+    n = 1 << logn
+    batch = max(3, (1 << 16) // n) + 1
+    xr, xi = W.normal_planes(n, batch, seed=900 + logn + idx)
+    prev = S.sdft_schedule_selected(n, 0)
+    try:
+        assert S.sdft_schedule_select(n, 0, idx) == S.SDFT_OK
+        with Plan(n, batch) as plan:
+            assert S.sdft_schedule_describe(n, 0, idx).split(";")[0] in plan.describe()
+            for direction, fn in ((0, O.dft_factored_dit), (1, O.adjoint_factored)):
+                yr, yi = gpu_run(xr, xi, direction, plan=plan)
+                assert rel_l2_rows(yr, yi, *fn(xr, xi)).max() <= TOL_F32
+    finally:
+        S.sdft_schedule_select(n, 0, prev)
+
+
+def test_autotune_picks_a_schedule():
+    from paper_2504_07264_gb300 import autotune as A
+    from paper_2504_07264_gb300 import sdft as S
+    prev = S.sdft_schedule_selected(4096, 0)
+    try:
+        rec = A.tune_one(4096, points=1 << 22, reps=3)
+        assert 0 <= rec["index"] < S.sdft_schedule_count(4096, 0)
+        assert len(rec["ms"]) == S.sdft_schedule_count(4096, 0) and min(rec["ms"]) > 0
+        assert rec["ms"][rec["index"]] == min(rec["ms"])
+        assert S.sdft_schedule_selected(4096, 0) == rec["index"]
+    finally:
+        S.sdft_schedule_select(4096, 0, prev)
