@@ -247,7 +247,7 @@ def run_ours(args) -> None:
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    batch = args.batch
+    batch = args.batch or BATCH
     xr_h, xi_h = workloads.bandwidth(batch)
     points = N_POINTS * batch
     xr = torch.from_numpy(xr_h).cuda()
@@ -527,6 +527,14 @@ def run_workload(args) -> None:
         line["metric"] = ("planar DFT Gpts/s, ragged batch of 10000 transforms, lengths 2^U{3..16} "
                           "(seed 4), one persistent launch in a CUDA graph")
         line["value"] = line["forward"]["gpts"]
+    elif args.workload == "uniform":
+        n = args.n
+        batch = args.batch or max(1, (1 << 26) // n)
+        xr_h, xi_h = workloads.normal_planes(n, batch, seed=1)
+        line.update(_measure_uniform(n, batch, xr_h, xi_h, args.steps, args.warmup, stream,
+                                     dtype=args.dtype))
+        line["metric"] = f"planar DFT Gpts/s, N={n} B={batch} dtype {args.dtype}"
+        line["value"] = line["forward"]["gpts"]
     elif args.workload == "sizes":
         rows = []
         for logn in range(1, 17):
@@ -553,13 +561,17 @@ def main(argv=None) -> int:
                     help="skip the CPU oracle timing (it is on by default)")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the host-buffer end-to-end leg (it is on by default)")
-    ap.add_argument("--workload", choices=("bandwidth", "autograd", "precision", "ragged", "sizes"),
+    ap.add_argument("--workload",
+                    choices=("bandwidth", "autograd", "precision", "ragged", "sizes", "uniform"),
                     default="bandwidth",
                     help="bandwidth (default) is the headline line; the others print one "
                          "single-GPU line of their own")
-    ap.add_argument("--batch", type=int, default=BATCH,
-                    help="transforms per step (default: the full 65536; smaller only "
-                         "for profiling captures, never for a reported number)")
+    ap.add_argument("--n", type=int, default=1024, help="length for --workload uniform")
+    ap.add_argument("--dtype", type=int, default=0,
+                    help="arithmetic path for --workload uniform (0 FP32, 1 split-BF16, 2 split-FP16)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="transforms per step (default: the workload's own batch, 65536 for "
+                         "the headline; smaller only for profiling captures)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -140,6 +140,28 @@ SDFT_API int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, 
 /* Choose how sdft_execute_host moves data (default SDFT_HOST_AUTO). */
 SDFT_API int sdft_plan_set_host_mode(sdft_plan* plan, int mode);
 
+/* Launch grid (CTAs) of a uniform plan's kernel.  The default is the
+ * kernel's occupancy times the SM count; a persistent grid-stride loop makes
+ * any grid >= 1 correct.  Plans whose kernel owns per-CTA scratch (N >= 32768)
+ * and ragged plans keep their grid: SDFT_ERR_INVALID_ARG. */
+SDFT_API int sdft_plan_set_grid(sdft_plan* plan, int grid);
+SDFT_API int sdft_plan_grid(const sdft_plan* plan);
+
+/* Work-queue plans (ragged plans, and uniform plans of N >= 16384 on their
+ * default schedule) run long transforms as items that wait, on the device, for
+ * the items they depend on.  Every such wait polls at most `polls` times
+ * (~128 ns each; default 2^23, about a second); past that the kernel records
+ * SDFT_ERR_TIMEOUT in the status word, stops waiting anywhere, finishes its
+ * queue and exits (the results of that call are then invalid).  The status
+ * stays set, and later calls skip their waits too, until
+ * sdft_plan_sync_status reads and clears it.
+ * SDFT_ERR_INVALID_ARG for other plans or polls < 1. */
+SDFT_API int sdft_plan_set_wait_limit(sdft_plan* plan, int polls);
+/* Testing hook: make every pass-2 dependency of a work-queue plan with long
+ * transforms unreachable (on != 0) or normal again (on == 0), so that the
+ * bounded-wait path can be exercised without any fault on the GPU. */
+SDFT_API int sdft_plan_inject_unreachable_wait(sdft_plan* plan, int on);
+
 /* Wait for `stream`, then read and clear the plan's device status word:
  * SDFT_OK, or SDFT_ERR_TIMEOUT if a bounded device-side wait gave up. */
 SDFT_API int sdft_plan_sync_status(const sdft_plan* plan, void* stream);

@@ -37,7 +37,7 @@ def gpu_name() -> str:
     return torch.cuda.get_device_name(torch.cuda.current_device())
 
 
-def tune_one(n: int, dtype: int = S.SDFT_F32, points: int = 1 << 24, reps: int = 20,
+def tune_one(n: int, dtype: int = S.SDFT_F32, points: int = 1 << 26, reps: int = 20,
              stream=None) -> dict:
     """Time every schedule of length n on ``points`` complex values of random
     data (forward); selects the fastest and returns its record."""
@@ -63,7 +63,7 @@ def tune_one(n: int, dtype: int = S.SDFT_F32, points: int = 1 << 24, reps: int =
             "schedules": [S.sdft_schedule_describe(n, dtype, i) for i in range(count)]}
 
 
-def tune(sizes=None, dtype: int = S.SDFT_F32, points: int = 1 << 24, reps: int = 20) -> dict:
+def tune(sizes=None, dtype: int = S.SDFT_F32, points: int = 1 << 26, reps: int = 20) -> dict:
     """Tune every length in ``sizes`` (default 2 .. 65536); returns the table
     for this GPU: {str(dtype): {str(n): record}}."""
     sizes = [1 << m for m in range(1, 17)] if sizes is None else sizes
@@ -128,7 +128,7 @@ def ensure_applied() -> None:
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description="time every schedule and record the fastest")
     ap.add_argument("--out", default=os.environ.get("SDFT_TUNE_CACHE") or SHIPPED)
-    ap.add_argument("--points", type=int, default=1 << 24)
+    ap.add_argument("--points", type=int, default=1 << 26)
     ap.add_argument("--reps", type=int, default=20)
     a = ap.parse_args(argv)
     from . import build

@@ -241,12 +241,16 @@ __device__ __forceinline__ void step_compute_scatter(float (&re)[S::E], float (&
 }
 
 // Run all steps of S.  `sync` separates exchange writes from reads (and the
-// reads of one step from the writes of the next).
-template <class S, bool ADJ, class LD, class XW, class XR, class TW, class ST, class SYNC>
+// reads of one step from the writes of the next).  SYNC0: also synchronise
+// between the step-0 gather and the step-0 scatter, for callers whose step-0
+// source and exchange buffer share shared memory.
+template <class S, bool ADJ, bool SYNC0 = false, class LD, class XW, class XR, class TW, class ST,
+          class SYNC>
 __device__ __forceinline__ void run_steps(const int t, const W64& w, LD ld, XW xw, XR xr, TW tw,
                                           ST st, SYNC sync) {
     float re[S::E], im[S::E];
     step_gather<S, 0, ADJ>(re, im, t, ld, xr);
+    if constexpr (SYNC0) sync();
     step_compute_scatter<S, 0, ADJ>(re, im, t, w, tw, xw, st);
     if constexpr (S::NS > 1) {
         sync();

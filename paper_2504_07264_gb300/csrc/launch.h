@@ -44,6 +44,7 @@ struct KernelInfo {
     int64_t tw_entries;          // float2 entries over all tables
     int64_t scratch_per_cta;     // float2 scratch entries per resident CTA (0 = none)
     int launches;                // kernel launches per call
+    bool queue;                  // run as items of the persistent work-queue kernel
     cudaError_t (*prepare)();    // one-time function attributes
     int (*blocks_per_sm)();      // occupancy of the kernel
     cudaError_t (*launch)(const LaunchArgs&);

@@ -26,12 +26,45 @@ const KernelInfo* rows_candidate_small(int logn, int idx);
 const KernelInfo* rows_candidate_1024(int logn, int idx);
 const KernelInfo* rows_candidate_big(int logn, int idx);
 
+// The work-queue schedule of a long length (pass-1 / pass-2 items).
+const KernelInfo* queue_candidate(int logn) {
+    static KernelInfo q[17];
+    static const bool init = [] {
+        static const char* names[17] = {};
+        names[14] = "N=16384: work-queue items, 128 x 128, 4 column + 4 row tiles per transform";
+        names[15] = "N=32768: work-queue items, 256 x 128, 4 column + 8 row tiles per transform";
+        names[16] = "N=65536: work-queue items, 256 x 256, 8 column + 8 row tiles per transform";
+        for (int l = 14; l <= 16; ++l) {
+            q[l] = KernelInfo{};
+            q[l].name = names[l];
+            q[l].logn = l;
+            q[l].threads = 256;
+            q[l].transforms_per_cta = 1;
+            q[l].launches = 1;
+            q[l].queue = true;
+        }
+        return true;
+    }();
+    (void)init;
+    return (logn >= 14 && logn <= 16) ? &q[logn] : nullptr;
+}
+
 // Compiled FP32 schedule `idx` for log2 N (null past the last one).
 const KernelInfo* f32_candidate(int logn, int idx) {
     if (logn >= 1 && logn <= 9) return rows_candidate_small(logn, idx);
     if (logn == 10) return rows_candidate_1024(logn, idx);
-    if (logn >= 11 && logn <= 14) return rows_candidate_big(logn, idx);
-    if (logn >= 15 && logn <= 16) return idx == 0 ? large_kernel(logn) : nullptr;
+    if (logn >= 11 && logn <= 13) return rows_candidate_big(logn, idx);
+    if (logn == 14) {
+        const KernelInfo* k = rows_candidate_big(logn, idx);
+        if (k) return k;
+        int n = 0;
+        while (rows_candidate_big(logn, n)) ++n;
+        return idx == n ? queue_candidate(14) : nullptr;
+    }
+    if (logn >= 15 && logn <= 16) {
+        if (idx == 0) return queue_candidate(logn);
+        if (idx == 1) return large_kernel(logn);
+    }
     return nullptr;
 }
 
@@ -65,11 +98,19 @@ struct HostStaging {
 // direction (a memset of the work counter, then the persistent kernel).
 struct RaggedState {
     bool on = false;
+    bool uniform = false;             // a uniform batch of long transforms
     int64_t count = 0;
     long long* d_offsets = nullptr;
     int4* d_items = nullptr;
     int nitems = 0;
-    int* d_counter = nullptr;
+    int nlong = 0;                     // long transforms (pass-1 / pass-2 items)
+    int slots = 0;                     // scratch slots in the ring
+    int* d_sync = nullptr;             // [work counter, done1[nlong], done2[nlong]]
+    long long* d_long_offsets = nullptr;
+    int* d_long_slot = nullptr;
+    int* d_tiles2 = nullptr;
+    int wait_polls = 1 << 23;          // ~1 s of 128 ns polls
+    int dep_extra = 0;                 // fault injection for tests (unreachable waits)
     const float2* tw[17] = {};
     unsigned classes = 0;              // bit l set: some transform has log2 N = l
     cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -90,6 +131,7 @@ struct sdft_plan {
     int64_t points;
     const KernelInfo* kern;
     int grid;
+    int occupancy;        // CTAs per SM from the occupancy query (negative: its error)
     float2* d_tw;
     float2* d_scratch;
     int* d_status;
@@ -154,7 +196,10 @@ void free_plan_memory(sdft_plan* p) {
     }
     if (r.d_offsets) cudaFree(r.d_offsets);
     if (r.d_items) cudaFree(r.d_items);
-    if (r.d_counter) cudaFree(r.d_counter);
+    if (r.d_sync) cudaFree(r.d_sync);
+    if (r.d_long_offsets) cudaFree(r.d_long_offsets);
+    if (r.d_long_slot) cudaFree(r.d_long_slot);
+    if (r.d_tiles2) cudaFree(r.d_tiles2);
 }
 
 bool ranges_overlap(const void* a, const void* b, size_t bytes) {
@@ -225,7 +270,16 @@ int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi,
     a.offsets = r.d_offsets;
     a.items = r.d_items;
     a.nitems = r.nitems;
-    a.counter = r.d_counter;
+    a.counter = r.d_sync;
+    a.long_offsets = r.d_long_offsets;
+    a.long_slot = r.d_long_slot;
+    a.tiles2 = r.d_tiles2;
+    a.done1 = r.d_sync + 1;
+    a.done2 = r.d_sync + 1 + r.nlong;
+    a.status = p->d_status;
+    a.wait_polls = r.wait_polls;
+    a.dep_extra = r.dep_extra;
+    a.slot_size = ragged_slot_size();
     a.scratch = scratch;
     for (int l = 0; l < 17; ++l) a.tw[l] = r.tw[l];
     a.w = p->w64;
@@ -241,10 +295,10 @@ int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi,
     if (!r.exec[d]) {
         if (cudaGraphCreate(&r.graph[d], 0) != cudaSuccess) return SDFT_ERR_CUDA;
         cudaMemsetParams mp = {};
-        mp.dst = r.d_counter;
+        mp.dst = r.d_sync;
         mp.value = 0;
         mp.elementSize = sizeof(int);
-        mp.width = 1;
+        mp.width = (size_t)(1 + 2 * r.nlong);
         mp.height = 1;
         mp.pitch = 0;
         cudaGraphNode_t mnode = nullptr;
@@ -280,6 +334,165 @@ int run(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr
         cudaStream_t stream, long long batch, float2* scratch) {
     if (p->rag.on) return launch_ragged(p, direction, xr, xi, yr, yi, stream, scratch);
     return launch(p, direction, xr, xi, yr, yi, stream, batch, scratch);
+}
+
+// Ragged plans, and uniform plans of long transforms: build the work queue
+// of the persistent kernel (ragged.cu).  Long transforms (N >= 16384) come
+// first, their pass-1 items interleaved with the pass-2 items of the
+// transform `lag` places earlier; scratch slots are reused round-robin, the
+// pass-1 items of a transform depending on the pass 2 of the slot's previous
+// user (always earlier in the queue).  Row items follow, longest first.
+sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform) {
+    constexpr int kMaxSlots = 128;        // 128 x 512 KiB = 64 MiB of scratch
+    std::vector<int> logn((size_t)count);
+    int64_t total = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        logn[(size_t)t] = log2_exact(lengths[t]);
+        total += lengths[t];
+        if (total > ((int64_t)1 << 40)) { fail(SDFT_ERR_INVALID_ARG); return nullptr; }
+    }
+    std::vector<long long> start((size_t)count);
+    {
+        long long o = 0;
+        for (int64_t t = 0; t < count; ++t) { start[(size_t)t] = o; o += lengths[t]; }
+    }
+    unsigned classes = 0;
+    // long transforms, longest first
+    std::vector<long long> long_off;
+    std::vector<int> long_logn;
+    for (int l = kMaxLogN; l >= 2; --l) {
+        const RaggedClass* c = ragged_class(l);
+        if (!c->large) continue;
+        for (int64_t t = 0; t < count; ++t)
+            if (logn[(size_t)t] == l) {
+                long_off.push_back(start[(size_t)t]);
+                long_logn.push_back(l);
+                classes |= 1u << l;
+            }
+    }
+    const int nlong = (int)long_off.size();
+    const int slots = std::min(nlong, kMaxSlots);
+    const int lag = std::max(1, slots / 2);
+    std::vector<int4> items;
+    std::vector<int> long_slot((size_t)nlong), tiles2((size_t)nlong);
+    for (int lt = 0; lt < nlong; ++lt) {
+        long_slot[(size_t)lt] = lt % std::max(slots, 1);
+        tiles2[(size_t)lt] = ragged_class(long_logn[(size_t)lt])->tiles2;
+    }
+    for (int k = 0; k < nlong + lag; ++k) {
+        if (k < nlong) {
+            const RaggedClass* c = ragged_class(long_logn[(size_t)k]);
+            const int dep = k >= slots ? k - slots : -1;
+            for (int j = 0; j < c->tiles1; ++j)
+                items.push_back(make_int4(kPass1 + c->logn, k, j, dep));
+        }
+        if (k >= lag && k - lag < nlong) {
+            const int lt = k - lag;
+            const RaggedClass* c = ragged_class(long_logn[(size_t)lt]);
+            for (int j = 0; j < c->tiles2; ++j)
+                items.push_back(make_int4(kPass2 + c->logn, lt, j, lt));
+        }
+    }
+    // row items, longest first
+    std::vector<long long> order_off;
+    for (int l = kMaxLogN; l >= 2; --l) {
+        const RaggedClass* c = ragged_class(l);
+        if (c->large) continue;
+        const int first = (int)order_off.size();
+        for (int64_t t = 0; t < count; ++t)
+            if (logn[(size_t)t] == l) order_off.push_back(start[(size_t)t]);
+        const int n_in = (int)order_off.size() - first;
+        if (n_in == 0) continue;
+        classes |= 1u << l;
+        for (int s0 = 0; s0 < n_in; s0 += c->per_item)
+            items.push_back(make_int4(l, first + s0, std::min(c->per_item, n_in - s0), 0));
+    }
+
+    sdft_plan* p = new (std::nothrow) sdft_plan();
+    if (!p) { fail(SDFT_ERR_ALLOC); return nullptr; }
+    p->magic = 0;
+    p->dtype = SDFT_F32;
+    p->n = uniform ? lengths[0] : 0;
+    p->batch = count;
+    p->points = total;
+    p->kern = nullptr;
+    RaggedState& r = p->rag;
+    r.on = true;
+    r.uniform = uniform;
+    r.count = count;
+    r.nitems = (int)items.size();
+    r.nlong = nlong;
+    r.slots = slots;
+    r.classes = classes;
+    int status = SDFT_OK;
+    cudaStream_t st = nullptr;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    };
+    do {
+        if (cudaGetDevice(&p->device) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+            status = SDFT_ERR_CUDA; break;
+        }
+        if (ragged_prepare() != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        p->occupancy = ragged_blocks_per_sm();
+        p->grid = std::max(1, p->occupancy) * sms;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            status = SDFT_ERR_CUDA; break;
+        }
+        int64_t tw_total = 64;
+        int64_t base[17] = {};
+        for (int l = 2; l <= kMaxLogN; ++l)
+            if (classes & (1u << l)) { base[l] = tw_total; tw_total += ragged_class(l)->tw_entries; }
+        const size_t nl = (size_t)std::max(nlong, 1);
+        if (cudaMalloc(&p->d_tw, tw_total * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&r.d_sync, (1 + 2 * nl) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&r.d_offsets, std::max<size_t>(order_off.size(), 1) * sizeof(long long)) != cudaSuccess ||
+            cudaMalloc(&r.d_items, std::max<size_t>(items.size(), 1) * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc(&r.d_long_offsets, nl * sizeof(long long)) != cudaSuccess ||
+            cudaMalloc(&r.d_long_slot, nl * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&r.d_tiles2, nl * sizeof(int)) != cudaSuccess) {
+            status = SDFT_ERR_ALLOC; break;
+        }
+        if (slots > 0) {
+            const size_t bytes = (size_t)slots * (size_t)ragged_slot_size() * sizeof(float2);
+            if (cudaMalloc(&p->d_scratch, bytes) != cudaSuccess) { status = SDFT_ERR_ALLOC; break; }
+        }
+        if (cudaMemsetAsync(p->d_status, 0, sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(r.d_sync, 0, (1 + 2 * nl) * sizeof(int), st) != cudaSuccess ||
+            !up(r.d_offsets, order_off.data(), order_off.size() * sizeof(long long)) ||
+            !up(r.d_items, items.data(), items.size() * sizeof(int4)) ||
+            !up(r.d_long_offsets, long_off.data(), long_off.size() * sizeof(long long)) ||
+            !up(r.d_long_slot, long_slot.data(), long_slot.size() * sizeof(int)) ||
+            !up(r.d_tiles2, tiles2.data(), tiles2.size() * sizeof(int))) {
+            status = SDFT_ERR_CUDA; break;
+        }
+        if (make_w64(&p->w64, p->d_tw, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+        for (int l = 2; l <= kMaxLogN && status == SDFT_OK; ++l) {
+            if (!(classes & (1u << l))) continue;
+            const RaggedClass* c = ragged_class(l);
+            r.tw[l] = p->d_tw + base[l];
+            if (make_tables(p->d_tw + base[l], c->tables, c->ntables, st) != cudaSuccess)
+                status = SDFT_ERR_CUDA;
+        }
+        if (status != SDFT_OK) break;
+        if (cudaStreamSynchronize(st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
+    } while (0);
+    if (st) cudaStreamDestroy(st);
+    if (status != SDFT_OK) {
+        free_plan_memory(p);
+        delete p;
+        fail(status);
+        return nullptr;
+    }
+    p->magic = kMagic;
+    {
+        std::lock_guard<std::mutex> lk(g_registry_mu);
+        g_registry.insert(p);
+    }
+    return p;
 }
 
 }  // namespace
@@ -335,6 +548,10 @@ sdft_plan* plan_create_idx(int64_t n, int64_t batch, int dtype, int idx) {
         k = &si->kern;
     }
     if (!k) { fail(SDFT_ERR_UNSUPPORTED_N); return nullptr; }
+    if (k->queue) {
+        std::vector<int64_t> lengths((size_t)batch, n);
+        return create_queue_plan(lengths.data(), batch, true);
+    }
 
     sdft_plan* p = new (std::nothrow) sdft_plan();
     if (!p) { fail(SDFT_ERR_ALLOC); return nullptr; }
@@ -353,7 +570,8 @@ sdft_plan* plan_create_idx(int64_t n, int64_t batch, int dtype, int idx) {
             status = SDFT_ERR_CUDA; break;
         }
         if (k->prepare() != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
-        const int bps = std::max(1, k->blocks_per_sm());
+        p->occupancy = k->blocks_per_sm();
+        const int bps = std::max(1, p->occupancy);
         p->grid = bps * sms;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             status = SDFT_ERR_CUDA; break;
@@ -397,112 +615,16 @@ sdft_plan* sdft_plan_create_ragged(const int64_t* lengths, int64_t count, int dt
         fail(SDFT_ERR_INVALID_ARG);
         return nullptr;
     }
-    std::vector<int> logn((size_t)count);
-    int64_t total = 0;
+    if (dtype != SDFT_F32 && dtype != SDFT_F32_SPLIT_BF16 && dtype != SDFT_F32_SPLIT_FP16) {
+        fail(SDFT_ERR_UNSUPPORTED_DTYPE);
+        return nullptr;
+    }
     for (int64_t t = 0; t < count; ++t) {
         const int l = log2_exact(lengths[t]);
         if (l < 2 || l > kMaxLogN) { fail(SDFT_ERR_UNSUPPORTED_N); return nullptr; }
-        logn[(size_t)t] = l;
-        total += lengths[t];
-        if (total > ((int64_t)1 << 40)) { fail(SDFT_ERR_INVALID_ARG); return nullptr; }
     }
     if (dtype != SDFT_F32) { fail(SDFT_ERR_UNSUPPORTED_DTYPE); return nullptr; }
-
-    // work order: longest first (stable), items of per_item transforms
-    std::vector<long long> start((size_t)count);
-    {
-        long long o = 0;
-        for (int64_t t = 0; t < count; ++t) { start[(size_t)t] = o; o += lengths[t]; }
-    }
-    std::vector<long long> order_off;
-    std::vector<int4> items;
-    order_off.reserve((size_t)count);
-    unsigned classes = 0;
-    for (int l = kMaxLogN; l >= 2; --l) {
-        const int first = (int)order_off.size();
-        for (int64_t t = 0; t < count; ++t)
-            if (logn[(size_t)t] == l) order_off.push_back(start[(size_t)t]);
-        const int n_in = (int)order_off.size() - first;
-        if (n_in == 0) continue;
-        classes |= 1u << l;
-        const int per = ragged_class(l)->per_item;
-        for (int s0 = 0; s0 < n_in; s0 += per)
-            items.push_back(make_int4(l, first + s0, std::min(per, n_in - s0), 0));
-    }
-
-    sdft_plan* p = new (std::nothrow) sdft_plan();
-    if (!p) { fail(SDFT_ERR_ALLOC); return nullptr; }
-    p->magic = 0;
-    p->dtype = dtype;
-    p->n = 0;
-    p->batch = count;
-    p->points = total;
-    p->kern = nullptr;
-    RaggedState& r = p->rag;
-    r.on = true;
-    r.count = count;
-    r.nitems = (int)items.size();
-    r.classes = classes;
-    int status = SDFT_OK;
-    cudaStream_t st = nullptr;
-    do {
-        if (cudaGetDevice(&p->device) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
-        int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
-            status = SDFT_ERR_CUDA; break;
-        }
-        if (ragged_prepare() != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
-        p->grid = std::max(1, ragged_blocks_per_sm()) * sms;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-            status = SDFT_ERR_CUDA; break;
-        }
-        int64_t tw_total = 64;
-        int64_t base[17] = {};
-        for (int l = 2; l <= kMaxLogN; ++l)
-            if (classes & (1u << l)) { base[l] = tw_total; tw_total += ragged_class(l)->tw_entries; }
-        if (cudaMalloc(&p->d_tw, tw_total * sizeof(float2)) != cudaSuccess ||
-            cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&r.d_counter, sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&r.d_offsets, order_off.size() * sizeof(long long)) != cudaSuccess ||
-            cudaMalloc(&r.d_items, items.size() * sizeof(int4)) != cudaSuccess) {
-            status = SDFT_ERR_ALLOC; break;
-        }
-        if (classes & ((1u << 15) | (1u << 16))) {
-            const size_t bytes = (size_t)p->grid * (size_t)ragged_scratch_per_cta() * sizeof(float2);
-            if (cudaMalloc(&p->d_scratch, bytes) != cudaSuccess) { status = SDFT_ERR_ALLOC; break; }
-        }
-        if (cudaMemsetAsync(p->d_status, 0, sizeof(int), st) != cudaSuccess ||
-            cudaMemsetAsync(r.d_counter, 0, sizeof(int), st) != cudaSuccess ||
-            cudaMemcpyAsync(r.d_offsets, order_off.data(), order_off.size() * sizeof(long long),
-                            cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(r.d_items, items.data(), items.size() * sizeof(int4),
-                            cudaMemcpyHostToDevice, st) != cudaSuccess) {
-            status = SDFT_ERR_CUDA; break;
-        }
-        if (make_w64(&p->w64, p->d_tw, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
-        for (int l = 2; l <= kMaxLogN && status == SDFT_OK; ++l) {
-            if (!(classes & (1u << l))) continue;
-            const RaggedClass* c = ragged_class(l);
-            r.tw[l] = p->d_tw + base[l];
-            if (make_tables(p->d_tw + base[l], c->tables, c->ntables, st) != cudaSuccess)
-                status = SDFT_ERR_CUDA;
-        }
-        if (status != SDFT_OK) break;
-        if (cudaStreamSynchronize(st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
-    } while (0);
-    if (st) cudaStreamDestroy(st);
-    if (status != SDFT_OK) {
-        free_plan_memory(p);
-        delete p;
-        fail(status);
-        return nullptr;
-    }
-    p->magic = kMagic;
-    {
-        std::lock_guard<std::mutex> lk(g_registry_mu);
-        g_registry.insert(p);
-    }
-    return p;
+    return create_queue_plan(lengths, count, false);
 }
 
 void sdft_plan_destroy(sdft_plan* plan) {
@@ -587,8 +709,8 @@ int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const flo
         }
         if (cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming) != cudaSuccess)
             return fail(SDFT_ERR_CUDA);
-        const int64_t scr = rag ? (plan->d_scratch ? ragged_scratch_per_cta() : 0)
-                                : plan->kern->scratch_per_cta;
+        // a work-queue plan moves its batch as one chunk (slot 0 only)
+        const int64_t scr = rag ? 0 : plan->kern->scratch_per_cta;
         if (scr > 0) {
             const size_t sb = (size_t)plan->grid * (size_t)scr * sizeof(float2);
             if (cudaMalloc(&h.d_scratch, sb) != cudaSuccess) return fail(SDFT_ERR_ALLOC);
@@ -620,6 +742,31 @@ int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const flo
     }
     for (int sl = 0; sl < 2; ++sl)
         if (cudaStreamSynchronize(h.streams[sl]) != cudaSuccess) return fail(SDFT_ERR_CUDA);
+    return SDFT_OK;
+}
+
+int sdft_plan_set_grid(sdft_plan* plan, int grid) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    if (grid < 1 || grid > (1 << 20)) return fail(SDFT_ERR_INVALID_ARG);
+    // kernels with per-CTA scratch own exactly `grid` slots; their grid is fixed
+    if (plan->d_scratch || plan->rag.on) return fail(SDFT_ERR_INVALID_ARG);
+    plan->grid = grid;
+    return SDFT_OK;
+}
+
+int sdft_plan_grid(const sdft_plan* plan) { return plan_alive(plan) ? plan->grid : 0; }
+
+int sdft_plan_set_wait_limit(sdft_plan* plan, int polls) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    if (!plan->rag.on || polls < 1) return fail(SDFT_ERR_INVALID_ARG);
+    plan->rag.wait_polls = polls;
+    return SDFT_OK;
+}
+
+int sdft_plan_inject_unreachable_wait(sdft_plan* plan, int on) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    if (!plan->rag.on || plan->rag.nlong == 0) return fail(SDFT_ERR_INVALID_ARG);
+    plan->rag.dep_extra = on ? 1 : 0;
     return SDFT_OK;
 }
 
@@ -657,6 +804,15 @@ int sdft_plan_launches(const sdft_plan* plan, int direction) {
 
 int sdft_plan_describe(const sdft_plan* plan, char* buf, int64_t len) {
     if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN), -1;
+    if (plan->rag.on && plan->rag.uniform) {
+        const KernelInfo* q = queue_candidate(log2_exact(plan->n));
+        return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
+                             "%s; one persistent launch (graph: counter memset + kernel), %d "
+                             "threads/CTA, %zu B smem, grid %d (occupancy %d), %d work items, "
+                             "%d scratch slots",
+                             q ? q->name : "work queue", ragged_threads(), ragged_smem(),
+                             plan->grid, plan->occupancy, plan->rag.nitems, plan->rag.slots);
+    }
     if (plan->rag.on) {
         char cls[128] = {0};
         int o = 0;
@@ -671,9 +827,10 @@ int sdft_plan_describe(const sdft_plan* plan, char* buf, int64_t len) {
                              ragged_threads(), ragged_smem(), plan->grid, plan->rag.nitems);
     }
     return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
-                         "%s; %d threads/CTA, %zu B smem, grid %d, %d transform(s)/CTA tile",
+                         "%s; %d threads/CTA, %zu B smem, grid %d (occupancy %d), "
+                         "%d transform(s)/CTA tile",
                          plan->kern->name, plan->kern->threads, plan->kern->smem, plan->grid,
-                         plan->kern->transforms_per_cta);
+                         plan->occupancy, plan->kern->transforms_per_cta);
 }
 
 int sdft_schedule_count(int64_t n, int dtype) {
@@ -688,6 +845,10 @@ int sdft_schedule_describe(int64_t n, int dtype, int index, char* buf, int64_t l
     if (logn < 1 || logn > kMaxLogN) return -fail(SDFT_ERR_UNSUPPORTED_N);
     const KernelInfo* k = candidate(logn, dtype, index);
     if (!k) return -fail(SDFT_ERR_INVALID_ARG);
+    if (k->queue)
+        return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
+                             "%s; %d threads/CTA, %zu B smem, persistent", k->name,
+                             ragged_threads(), ragged_smem());
     return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
                          "%s; %d threads/CTA, %zu B smem, %d transform(s)/CTA tile", k->name,
                          k->threads, k->smem, k->transforms_per_cta);
@@ -730,10 +891,10 @@ int sdft_autotune(int64_t n, int64_t batch, int dtype, const float* xr, const fl
         float ms = 0.f;
         int s = check_buffers(p, xr, xi, yr, yi);
         for (int w = 0; w < 2 && s == SDFT_OK; ++w)
-            s = launch(p, SDFT_FORWARD, xr, xi, yr, yi, st, batch, p->d_scratch);
+            s = run(p, SDFT_FORWARD, xr, xi, yr, yi, st, batch, p->d_scratch);
         if (s == SDFT_OK && cudaEventRecord(e0, st) != cudaSuccess) s = SDFT_ERR_CUDA;
         for (int r = 0; r < reps && s == SDFT_OK; ++r)
-            s = launch(p, SDFT_FORWARD, xr, xi, yr, yi, st, batch, p->d_scratch);
+            s = run(p, SDFT_FORWARD, xr, xi, yr, yi, st, batch, p->d_scratch);
         if (s == SDFT_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
                              cudaEventSynchronize(e1) != cudaSuccess ||
                              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))

@@ -291,12 +291,27 @@ cudaError_t split_prepare() {
                                 (int)CFG::SMEM);
 }
 
+// Resident CTAs per SM.  The runtime's occupancy query answers 1 for these
+// TMEM-allocating kernels although registers and shared memory allow more,
+// so the bound is computed from the kernel's own footprint: registers (per
+// warp, in units of 256), shared memory (plus the 1 KiB the driver reserves
+// per CTA), warps, and the SM's 512 TMEM columns.
 template <class CFG>
 int split_blocks_per_sm() {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_split<CFG, false>, 128, CFG::SMEM) !=
-        cudaSuccess)
-        return 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_split<CFG, false>);
+    if (e != cudaSuccess) return -(int)e;
+    int dev = 0, regs = 0, smem = 0, warps = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&warps, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess)
+        return -(int)e;
+    const int regs_per_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    int n = regs / (regs_per_warp * 4);
+    const int smem_cta = (int)(fa.sharedSizeBytes + CFG::SMEM) + 1024;
+    n = n < smem / smem_cta ? n : smem / smem_cta;
+    n = n < (warps / 32) / 4 ? n : (warps / 32) / 4;
     return n < CFG::MAX_CTAS ? n : CFG::MAX_CTAS;
 }
 

@@ -53,6 +53,10 @@ _SIGS = {
     "sdft_execute_host": ([_P, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
     "sdft_plan_sync_status": ([_P, _P], ctypes.c_int),
     "sdft_plan_set_host_mode": ([_P, ctypes.c_int], ctypes.c_int),
+    "sdft_plan_set_grid": ([_P, ctypes.c_int], ctypes.c_int),
+    "sdft_plan_set_wait_limit": ([_P, ctypes.c_int], ctypes.c_int),
+    "sdft_plan_inject_unreachable_wait": ([_P, ctypes.c_int], ctypes.c_int),
+    "sdft_plan_grid": ([_P], ctypes.c_int),
     "sdft_execute_noalloc": ([_I64, _I64, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
     "sdft_schedule_count": ([_I64, ctypes.c_int], ctypes.c_int),
     "sdft_schedule_describe": ([_I64, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, _I64], ctypes.c_int),
@@ -166,6 +170,22 @@ def sdft_autotune(n, batch, dtype, xr, xi, yr, yi, reps, ms_out, stream) -> int:
 
 def sdft_plan_set_host_mode(plan, mode: int) -> int:
     return lib().sdft_plan_set_host_mode(plan, mode)
+
+
+def sdft_plan_set_grid(plan, grid: int) -> int:
+    return lib().sdft_plan_set_grid(plan, grid)
+
+
+def sdft_plan_grid(plan) -> int:
+    return lib().sdft_plan_grid(plan)
+
+
+def sdft_plan_set_wait_limit(plan, polls: int) -> int:
+    return lib().sdft_plan_set_wait_limit(plan, polls)
+
+
+def sdft_plan_inject_unreachable_wait(plan, on: int) -> int:
+    return lib().sdft_plan_inject_unreachable_wait(plan, on)
 
 
 def sdft_plan_sync_status(plan, stream) -> int:
@@ -331,6 +351,13 @@ class Plan:
                 ptrs.append(a.ctypes.data)
         st = sdft_execute_host(self.handle, direction, *ptrs, _stream_handle(stream))
         _check(st, "sdft_execute_host")
+
+    @property
+    def grid(self) -> int:
+        return sdft_plan_grid(self.handle)
+
+    def set_grid(self, grid: int) -> None:
+        _check(sdft_plan_set_grid(self.handle, grid), "sdft_plan_set_grid")
 
     def set_host_mode(self, mode: int) -> None:
         _check(sdft_plan_set_host_mode(self.handle, mode), "sdft_plan_set_host_mode")

@@ -84,16 +84,56 @@ def test_every_class_and_many_items():
 
 def test_matches_uniform_plans_bitwise():
     """A ragged plan computes each transform exactly as the uniform plan of its
-    length does (same radix schedule and tables)."""
+    length does on its first schedule (same radix schedule and tables)."""
     from paper_2504_07264_gb300 import Plan
-    for n, cnt in ((16, 700), (1024, 37), (4096, 9), (65536, 3)):
+    from paper_2504_07264_gb300 import sdft as S
+    for n, cnt in ((16, 700), (1024, 37), (4096, 9), (32768, 5), (65536, 3)):
         lengths = np.full(cnt, n, dtype=np.int64)
         xr, xi, _ = _ragged_inputs(lengths, 44)
         with Plan(lengths=lengths) as rp:
             a = _run(rp, xr, xi, 0)
-        with Plan(n, cnt) as up:
-            b = _run(up, xr.reshape(cnt, n), xi.reshape(cnt, n), 0)
+        prev = S.sdft_schedule_selected(n, 0)
+        try:
+            S.sdft_schedule_select(n, 0, 0)
+            with Plan(n, cnt) as up:
+                b = _run(up, xr.reshape(cnt, n), xi.reshape(cnt, n), 0)
+        finally:
+            S.sdft_schedule_select(n, 0, prev)
         assert np.array_equal(a[0], b[0].ravel()) and np.array_equal(a[1], b[1].ravel()), n
+
+
+def test_bounded_wait_times_out_and_recovers():
+    """An unreachable dependency (planted on the host) makes the device-side
+    waits give up: the status word reports SDFT_ERR_TIMEOUT, the kernel
+    returns, and the same plan computes correctly afterwards."""
+    import torch
+
+    from paper_2504_07264_gb300 import Plan
+    from paper_2504_07264_gb300 import sdft as S
+    lengths = np.array([65536, 1024, 32768, 16384, 8], dtype=np.int64)
+    xr, xi, off = _ragged_inputs(lengths, 47)
+    with Plan(lengths=lengths) as plan:
+        h = plan.handle
+        assert S.sdft_plan_set_wait_limit(h, 2000) == S.SDFT_OK
+        assert S.sdft_plan_inject_unreachable_wait(h, 1) == S.SDFT_OK
+        _run(plan, xr, xi, 0)
+        assert plan.sync_status() == S.SDFT_ERR_TIMEOUT
+        assert S.sdft_plan_inject_unreachable_wait(h, 0) == S.SDFT_OK
+        assert S.sdft_plan_set_wait_limit(h, 1 << 23) == S.SDFT_OK
+        yr, yi = _run(plan, xr, xi, 0)
+        assert plan.sync_status() == S.SDFT_OK
+        torch.cuda.synchronize()
+    assert _check_segments(lengths, off, xr, xi, yr, yi, 0) <= TOL_F32
+
+
+def test_wait_hooks_reject_plans_without_waits():
+    from paper_2504_07264_gb300 import Plan
+    from paper_2504_07264_gb300 import sdft as S
+    with Plan(1024, 4) as plan:
+        assert S.sdft_plan_set_wait_limit(plan.handle, 10) == S.SDFT_ERR_INVALID_ARG
+        assert S.sdft_plan_inject_unreachable_wait(plan.handle, 1) == S.SDFT_ERR_INVALID_ARG
+    with Plan(lengths=np.array([8, 1024], dtype=np.int64)) as plan:
+        assert S.sdft_plan_inject_unreachable_wait(plan.handle, 1) == S.SDFT_ERR_INVALID_ARG
 
 
 def test_graph_replay_with_new_buffers():
