@@ -45,19 +45,25 @@ N_POINTS = 1024
 BATCH = 65536
 BYTES_PER_POINT = 16          # algorithmic: 4 B each of xr, xi read and yr, yi written
 
-# DRAM bytes per launch of the timed kernels, from one ncu capture each
-# (profiles/), keyed by a hash of the kernel sources they were taken on; a
-# kernel changed since then reports traffic null.
-NCU_TRAFFIC = {}
+# Sources of the timed N = 1024 kernel: the traffic figure below is reported
+# only while they are unchanged since its ncu capture.
+HEADLINE_SOURCES = ("fft_core.cuh", "kernels_rows.cuh", "rows_1024.cu", "launch.h")
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one forward
+# launch of the full 65536 x 1024 workload, from one ncu capture
+# (profiles/fwd_n1024_bandwidth.md), with the source hash it was taken on.
+NCU_TRAFFIC = {
+    "fwd": {"bytes": 536.92e6 + 485.23e6, "hash": "e29cf756c6d8ac29",
+            "schedule": "N=1024: 32 threads/transform, radix [32,32]"},
+}
 
 
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2504_07264_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in HEADLINE_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 
@@ -229,6 +235,7 @@ def run_ours(args) -> None:
     import workloads
     from paper_2504_07264_gb300 import SDFT_ADJOINT, SDFT_FORWARD, Plan
     from paper_2504_07264_gb300 import build as cuda_build
+    from paper_2504_07264_gb300.sharding import max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -282,10 +289,8 @@ def run_ours(args) -> None:
             copy()
         ms_copy = _time_steps(copy, max(10, args.steps // 4), stream)
     clocks = clk.summary(m0, m1 if m1 > m0 else None)
-    if dist is not None:
-        t = torch.tensor([ms_fwd, ms_adj], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_fwd, ms_adj = t.tolist()
+    ms_fwd = max_over_ranks(ms_fwd, dist)
+    ms_adj = max_over_ranks(ms_adj, dist)
 
     # end to end through the C ABI on pinned host buffers: the default mode
     # (zero copy for page-locked buffers) and the staged copy pipeline
@@ -307,11 +312,7 @@ def run_ours(args) -> None:
                 plan.execute_host(SDFT_FORWARD, hxr, hxi, hyr, hyi, stream)
             barrier()
             sec = (time.perf_counter() - t0) / e2e_steps
-            if dist is not None:
-                t = torch.tensor([sec], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                sec = t.item()
-            e2e_modes[mode_name] = sec
+            e2e_modes[mode_name] = max_over_ranks(sec, dist)
         e2e_s = e2e_modes["zero_copy"]
     describe = plan.describe()
     plan.destroy()
@@ -325,7 +326,8 @@ def run_ours(args) -> None:
     achieved_adj = BYTES_PER_POINT * points / (ms_adj * 1e-3) / 1e9
     src_hash = _kernel_source_hash()
     tr = NCU_TRAFFIC.get("fwd")
-    traffic = tr["bytes"] if tr and tr.get("hash") == src_hash else None
+    traffic = (tr["bytes"] if tr and tr.get("hash") == src_hash
+               and describe.startswith(tr["schedule"]) else None)
     cpu = None if args.no_cpu_baseline else cpu_oracle_rate()
     line = {
         "metric": METRIC,

@@ -93,17 +93,15 @@ __device__ __forceinline__ void item_pass2(const float* scr_re, const float* scr
     float* const x_re = sm;                  // exchange reuses the staging area
     float* const x_im = sm + C * TS;
     auto sync = [] { __syncthreads(); };
-    // stage TS contiguous slot rows (written by other SMs: bypass L1)
-    const float4* src_re = reinterpret_cast<const float4*>(scr_re + tile * TS * C);
-    const float4* src_im = reinterpret_cast<const float4*>(scr_im + tile * TS * C);
-    for (int u = (int)threadIdx.x; u < TS * C / 4; u += CFG::THREADS) {
-        const float4 a = __ldcg(src_re + u);
-        const float4 c = __ldcg(src_im + u);
-        const int row = (4 * u) / C, cc = (4 * u) % C;
-        float* dr = g_re + row * STG + cc;
-        float* di = g_im + row * STG + cc;
-        dr[0] = a.x; dr[1] = a.y; dr[2] = a.z; dr[3] = a.w;
-        di[0] = c.x; di[1] = c.y; di[2] = c.z; di[3] = c.w;
+    // stage TS contiguous slot rows (written by other SMs: bypass L1); one
+    // float per lane so that consecutive lanes write consecutive banks
+    const float* src_re = scr_re + tile * TS * C;
+    const float* src_im = scr_im + tile * TS * C;
+#pragma unroll 8
+    for (int u = (int)threadIdx.x; u < TS * C; u += CFG::THREADS) {
+        const int row = u / C, cc = u % C;
+        g_re[row * STG + cc] = __ldcg(src_re + u);
+        g_im[row * STG + cc] = __ldcg(src_im + u);
     }
     sync();
     const int d = tile * TS + sub;

@@ -10,7 +10,8 @@ const KernelInfo* rows_candidate_1024(int logn, int idx) {
         rows_info<RowCfg<10, 5, 5, 5, 0, 8, 0, 2>>("N=1024: 32 threads/transform, radix [32,32]"),
         rows_info<RowCfg<10, 5, 5, 5, 0, 8, 0, 2, true>>("N=1024: 32 threads/transform, radix [32,32], Eq. (6) order"),
         rows_info<RowCfg<10, 5, 5, 5, 0, 4, 0, 4>>("N=1024: 32 threads/transform, radix [32,32], 128-thread CTAs"),
-        rows_info<RowCfg<10, 4, 4, 3, 3, 4, 0, 4>>("N=1024: 64 threads/transform, radix [16,8,8]")};
+        rows_info<RowCfg<10, 4, 4, 3, 3, 4, 0, 4>>("N=1024: 64 threads/transform, radix [16,8,8]"),
+        rows_info<RowCfg<10, 4, 4, 4, 2, 4, 0, 4>>("N=1024: 64 threads/transform, radix [16,16,4]")};
     if (logn != 10 || idx < 0 || idx >= (int)(sizeof(k10) / sizeof(k10[0]))) return nullptr;
     return &k10[idx];
 }

@@ -343,7 +343,7 @@ int run(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr
 // pass-1 items of a transform depending on the pass 2 of the slot's previous
 // user (always earlier in the queue).  Row items follow, longest first.
 sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform) {
-    constexpr int kMaxSlots = 128;        // 128 x 512 KiB = 64 MiB of scratch
+    constexpr int kMaxSlots = 48;         // 48 x 512 KiB = 24 MiB of scratch, L2-resident
     std::vector<int> logn((size_t)count);
     int64_t total = 0;
     for (int64_t t = 0; t < count; ++t) {

@@ -167,17 +167,29 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
     const long long ntiles = (batch + TPT - 1) / TPT;
     const int bl = tid / R;          // transform within the tile
     const int c = tid % R;           // column (step 1) / output digit d (step 2)
+    // GEMM 1 operand of a tile: x[c + R * ntop] (zeros past the batch).  For
+    // R = 16 the next tile's values are loaded as soon as the current ones
+    // have been split into shared memory, so the loads overlap both GEMMs; for
+    // R = 32 the registers are needed by the GEMM-2 operands, so each tile
+    // loads its own values first.
+    float v[2 * R];
+    auto load_tile = [&](long long tile) {
+        const long long b = tile * TPT + bl;
+        const bool act = tile < ntiles && b < batch;
+        const long long base = (act ? b : 0) * (long long)N;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            v[t] = act ? xr[base + c + R * t] : 0.f;
+            v[R + t] = act ? xi[base + c + R * t] : 0.f;
+        }
+    };
+    constexpr bool kPrefetch = (R == 16);
+    if constexpr (kPrefetch) load_tile(blockIdx.x);
     for (long long tile = blockIdx.x; !bad && tile < ntiles; tile += gridDim.x) {
         const long long b = tile * TPT + bl;
         const bool active = b < batch;
         const long long base = (active ? b : 0) * (long long)N;
-        // ---- GEMM 1 operand: x[c + R * ntop], scaled and split
-        float v[2 * R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-            v[t] = active ? xr[base + c + R * t] : 0.f;
-            v[R + t] = active ? xi[base + c + R * t] : 0.f;
-        }
+        if constexpr (!kPrefetch) load_tile(tile);
         const int e0 = block_exponent<R>(v);
         const float s0 = ldexpf(1.f, -e0);
 #pragma unroll
@@ -188,6 +200,7 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
             *reinterpret_cast<uint16_t*>(a_hi + o) = h;
             *reinterpret_cast<uint16_t*>(a_lo + o) = l;
         }
+        if constexpr (kPrefetch) load_tile(tile + gridDim.x);
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();

@@ -57,7 +57,7 @@ def test_autotune_picks_a_schedule():
         rec = A.tune_one(4096, points=1 << 22, reps=3)
         assert 0 <= rec["index"] < S.sdft_schedule_count(4096, 0)
         assert len(rec["ms"]) == S.sdft_schedule_count(4096, 0) and min(rec["ms"]) > 0
-        assert rec["ms"][rec["index"]] == min(rec["ms"])
+        assert rec["ms"][rec["index"]] <= min(rec["ms"]) / (1 - 0.011)
         assert S.sdft_schedule_selected(4096, 0) == rec["index"]
     finally:
         S.sdft_schedule_select(4096, 0, prev)
