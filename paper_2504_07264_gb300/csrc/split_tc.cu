@@ -21,9 +21,13 @@
 // One CTA of 128 threads (a warpgroup) owns 128 GEMM rows = 128 / R
 // transforms per tile; thread i owns row i and TMEM lane i.  Thread 0 issues
 // the MMAs (6 per GEMM for R = 16, 12 for R = 32) and commits them to an
-// mbarrier; the block matrices (hi and lo) arrive once per CTA by a 1-D bulk
-// copy (TMA).  Operands are K-major, no swizzle: 8-row x 16-byte core
-// matrices, K-adjacent core matrices 128 B apart, 8-row groups K/8*128 B apart.
+// mbarrier.  Data moves in bulk (TMA, 1-D): the block matrices once per CTA,
+// each tile's input into a shared buffer -- the next tile's while the current
+// one is in its GEMMs -- and each tile's output from shared memory.  Operands
+// are K-major, no swizzle: 8-row x 16-byte core matrices, K-adjacent core
+// matrices 128 B apart, 8-row groups K/8*128 B apart; every thread writes its
+// row as 16-byte core-matrix rows.  The GEMM-2 operand is the GEMM-1 result
+// transposed per transform, which goes through a padded float32 buffer.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -48,16 +52,30 @@ struct SplitCfg {
     static constexpr int LBO = 128;             // bytes between K-adjacent core matrices
     static constexpr int A_BYTES = ROWS * K * 2;
     static constexpr int B_BYTES = NM * K * 2;
+    static constexpr int TILE_FLOATS = TPT * N;               // one plane of a tile
+    static constexpr int X_BYTES = 2 * TILE_FLOATS * 4;       // input tile, both planes
+    static constexpr int T_BYTES = 2 * ROWS * (R + 1) * 4;    // padded transpose buffer
+    // R = 16: the next tile's input is prefetched into its own buffer during
+    // the GEMMs.  R = 32: the input tile shares the operand region (loaded at
+    // the start of each tile), which keeps 4 CTAs per SM within shared memory.
+    static constexpr bool PREFETCH = (R == 16);
+    // the region holding the GEMM operands (A hi, A lo), then the transpose
+    // buffer, then the output tile (and for R = 32 first the input tile)
+    static constexpr int AREG_BYTES =
+        (2 * A_BYTES > T_BYTES ? (2 * A_BYTES > X_BYTES ? 2 * A_BYTES : X_BYTES)
+                               : (T_BYTES > X_BYTES ? T_BYTES : X_BYTES));
     static constexpr int TMEM_COLS = 2 * NM;    // D1 and D2 (64 or 128 columns)
     static constexpr int MAX_CTAS = 512 / TMEM_COLS;
     static constexpr int MINB = MAX_CTAS > 4 ? 4 : MAX_CTAS;
     static constexpr uint32_t IDESC = tc::idesc_f16(FP16, ROWS, NM);
-    // A hi, A lo, B hi, B lo, plus alignment slack; raised so that no more
-    // CTAs fit on an SM (228 KiB) than its 512 TMEM columns can serve.
-    static constexpr size_t NEED = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 1024;
+    static constexpr int OFF_X = 0, OFF_A = PREFETCH ? X_BYTES : 0, OFF_B = OFF_A + AREG_BYTES;
+    // x tile, operand region, B hi, B lo, plus alignment slack; raised so that
+    // no more CTAs fit on an SM (228 KiB) than its 512 TMEM columns can serve.
+    static constexpr size_t NEED = (size_t)OFF_B + 2 * (size_t)B_BYTES + 1024;
     static constexpr size_t FLOOR = (size_t)(228 * 1024) / (MAX_CTAS + 1) + 1024;
     static constexpr size_t SMEM = NEED > FLOOR ? NEED : FLOOR;
     static_assert(R == 16 || R == 32, "split path covers N = 256 and 1024");
+    static_assert(X_BYTES % 1024 == 0 && AREG_BYTES % 16 == 0, "alignment");
 };
 
 // byte offset of element (row, k) in a K-major, no-swizzle operand
@@ -76,6 +94,24 @@ __device__ __forceinline__ void split16(const float v, uint16_t& hi, uint16_t& l
         hi = __bfloat16_as_ushort(h);
         lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
     }
+}
+
+// Split 8 consecutive K values of a row into hi and lo parts and store them as
+// the row's 16-byte segment of one core matrix in each operand.
+template <bool FP16>
+__device__ __forceinline__ void store_row8(uint8_t* a_hi, uint8_t* a_lo, uint32_t off,
+                                           const float* v, float scale) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint16_t h0, l0, h1, l1;
+        split16<FP16>(v[2 * j] * scale, h0, l0);
+        split16<FP16>(v[2 * j + 1] * scale, h1, l1);
+        h[j] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+        l[j] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    }
+    *reinterpret_cast<uint4*>(a_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(a_lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // D (TMEM columns at dt) = A * B over the three split terms, small terms first.
@@ -125,29 +161,37 @@ __global__ void __launch_bounds__(128, CFG::MINB)
 k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         const uint16_t* __restrict__ bimg, const float2* __restrict__ tw, int* status) {
     constexpr int R = CFG::R, N = CFG::N, NM = CFG::NM, TPT = CFG::TPT;
+    constexpr int TF = CFG::TILE_FLOATS;
     extern __shared__ uint8_t smraw[];
     uint8_t* const sm = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t* const a_hi = sm;
-    uint8_t* const a_lo = sm + CFG::A_BYTES;
-    uint8_t* const b_hi = sm + 2 * CFG::A_BYTES;
-    uint8_t* const b_lo = b_hi + CFG::B_BYTES;
-    __shared__ __align__(8) uint64_t mbar[2];
+    float* const x_re = reinterpret_cast<float*>(sm + CFG::OFF_X);   // input tile
+    float* const x_im = x_re + TF;
+    uint8_t* const a_hi = sm + CFG::OFF_A;                            // GEMM operands
+    uint8_t* const a_lo = a_hi + CFG::A_BYTES;
+    float* const t_re = reinterpret_cast<float*>(sm + CFG::OFF_A);    // transpose (aliases A)
+    float* const t_im = t_re + CFG::ROWS * (R + 1);
+    float* const y_re = reinterpret_cast<float*>(sm + CFG::OFF_A);    // output tile (aliases A)
+    float* const y_im = y_re + TF;
+    uint8_t* const b_hi = sm + CFG::OFF_B;
+    __shared__ __align__(8) uint64_t mbar[3];
     __shared__ uint32_t tmem_base;
     const int tid = (int)threadIdx.x;
     const int warp = tid >> 5;
-    const uint32_t mb0 = tc::smem_u32(&mbar[0]);
-    const uint32_t mb1 = tc::smem_u32(&mbar[1]);
+    const uint32_t mb_mma = tc::smem_u32(&mbar[0]);
+    const uint32_t mb_b = tc::smem_u32(&mbar[1]);
+    const uint32_t mb_x = tc::smem_u32(&mbar[2]);
     const uint32_t sa_hi = tc::smem_u32(a_hi), sa_lo = tc::smem_u32(a_lo);
-    const uint32_t sb_hi = tc::smem_u32(b_hi), sb_lo = tc::smem_u32(b_lo);
+    const uint32_t sb_hi = tc::smem_u32(b_hi), sb_lo = sb_hi + CFG::B_BYTES;
 
     if (warp == 0) {
         tc::tmem_alloc(tc::smem_u32(&tmem_base), CFG::TMEM_COLS);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(mb0, 1);
-        tc::mbar_init(mb1, 1);
+        tc::mbar_init(mb_mma, 1);
+        tc::mbar_init(mb_b, 1);
+        tc::mbar_init(mb_x, 1);
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
@@ -156,107 +200,127 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
     const uint32_t tbase = tmem_base;
     const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
 
-    // the block matrices (hi then lo) of this direction, once per CTA
-    if (tid == 0) {
-        tc::mbar_expect_tx(mb1, 2 * CFG::B_BYTES);
-        tc::bulk_g2s(sb_hi, bimg + (ADJ ? CFG::B_BYTES : 0), 2 * CFG::B_BYTES, mb1);
-    }
-    int bad = __syncthreads_or(!tc::mbar_wait(mb1, 0));
-    uint32_t phase = 0;
-
     const long long ntiles = (batch + TPT - 1) / TPT;
+    // bulk-load tile `t`'s rows (both planes) into the input buffer
+    auto load_tile = [&](long long t) {
+        const long long first = t * TPT;
+        const long long cnt = (batch - first < TPT) ? (batch - first) : TPT;
+        const uint32_t bytes = (uint32_t)(cnt * N * 4);
+        tc::mbar_expect_tx(mb_x, 2 * bytes);
+        tc::bulk_g2s(tc::smem_u32(x_re), xr + first * N, bytes, mb_x);
+        tc::bulk_g2s(tc::smem_u32(x_im), xi + first * N, bytes, mb_x);
+    };
+    bool x_pending = false;          // thread 0: an input copy not yet waited for
+    if (tid == 0) {
+        // the block matrices (hi then lo) of this direction, once per CTA
+        tc::mbar_expect_tx(mb_b, 2 * CFG::B_BYTES);
+        tc::bulk_g2s(sb_hi, bimg + (ADJ ? CFG::B_BYTES : 0), 2 * CFG::B_BYTES, mb_b);
+        if (CFG::PREFETCH && blockIdx.x < ntiles) { load_tile(blockIdx.x); x_pending = true; }
+    }
+    int bad = __syncthreads_or(!tc::mbar_wait(mb_b, 0));
+    uint32_t ph_mma = 0, ph_x = 0;
+
     const int bl = tid / R;          // transform within the tile
-    const int c = tid % R;           // column (step 1) / output digit d (step 2)
-    // GEMM 1 operand of a tile: x[c + R * ntop] (zeros past the batch).  For
-    // R = 16 the next tile's values are loaded as soon as the current ones
-    // have been split into shared memory, so the loads overlap both GEMMs; for
-    // R = 32 the registers are needed by the GEMM-2 operands, so each tile
-    // loads its own values first.
-    float v[2 * R];
-    auto load_tile = [&](long long tile) {
-        const long long b = tile * TPT + bl;
-        const bool act = tile < ntiles && b < batch;
-        const long long base = (act ? b : 0) * (long long)N;
+    const int c = tid % R;           // column (GEMM 1 row) / output digit d (GEMM 2 row)
+    for (long long tile = blockIdx.x; !bad && tile < ntiles; tile += gridDim.x) {
+        const long long first = tile * TPT;
+        const long long cnt = (batch - first < TPT) ? (batch - first) : TPT;
+        // the previous tile's output store has finished reading the operand region
+        if (tid == 0) tc::bulk_wait_read0();
+        if constexpr (!CFG::PREFETCH) {
+            __syncthreads();
+            if (tid == 0) { load_tile(tile); x_pending = true; }
+        }
+        if (__syncthreads_or(!tc::mbar_wait(mb_x, ph_x))) { bad = 1; break; }
+        ph_x ^= 1;
+        x_pending = false;
+        // ---- GEMM 1 operand: row (b, c) = x[c + R * ntop], scaled and split
+        float v[2 * R];
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-            v[t] = act ? xr[base + c + R * t] : 0.f;
-            v[R + t] = act ? xi[base + c + R * t] : 0.f;
+            v[t] = x_re[bl * N + c + R * t];
+            v[R + t] = x_im[bl * N + c + R * t];
         }
-    };
-    constexpr bool kPrefetch = (R == 16);
-    if constexpr (kPrefetch) load_tile(blockIdx.x);
-    for (long long tile = blockIdx.x; !bad && tile < ntiles; tile += gridDim.x) {
-        const long long b = tile * TPT + bl;
-        const bool active = b < batch;
-        const long long base = (active ? b : 0) * (long long)N;
-        if constexpr (!kPrefetch) load_tile(tile);
         const int e0 = block_exponent<R>(v);
         const float s0 = ldexpf(1.f, -e0);
+        if constexpr (!CFG::PREFETCH) __syncthreads();   // input read before the operands overwrite it
 #pragma unroll
-        for (int k = 0; k < 2 * R; ++k) {
-            uint16_t h, l;
-            split16<CFG::FP16_>(v[k] * s0, h, l);
-            const uint32_t o = kmaj(tid, k, CFG::SBO);
-            *reinterpret_cast<uint16_t*>(a_hi + o) = h;
-            *reinterpret_cast<uint16_t*>(a_lo + o) = l;
-        }
-        if constexpr (kPrefetch) load_tile(tile + gridDim.x);
+        for (int k8 = 0; k8 < 2 * R / 8; ++k8)
+            store_row8<CFG::FP16_>(a_hi, a_lo, kmaj(tid, 8 * k8, CFG::SBO), v + 8 * k8, s0);
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
             issue_gemm<CFG>(tbase, sa_hi, sa_lo, sb_hi, sb_lo);
-            tc::mma_commit(mb0);
+            tc::mma_commit(mb_mma);
+            if (CFG::PREFETCH && tile + gridDim.x < ntiles) {              // prefetch
+                load_tile(tile + gridDim.x);
+                x_pending = true;
+            }
         }
-        if (__syncthreads_or(!tc::mbar_wait(mb0, phase))) { bad = 1; break; }
-        phase ^= 1;
+        if (__syncthreads_or(!tc::mbar_wait(mb_mma, ph_mma))) { bad = 1; break; }
+        ph_mma ^= 1;
         tc::fence_after_sync();
-        // ---- rotate row (b, c) by W_N^{c d}, rescale, split into GEMM 2 rows (b, d)
+        // ---- rotate row (b, c) by W_N^{c d}; transpose each transform (b)
         float d1[2 * R];
         tmem_row<R>(lane_base, d1);
 #pragma unroll
         for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], __ldg(tw + d * R + c));
-        const int e1 = block_exponent<R>(d1);
-        const float s1 = ldexpf(1.f, -e1);
 #pragma unroll
         for (int d = 0; d < R; ++d) {
-            uint16_t h, l;
-            const int row = bl * R + d;
-            split16<CFG::FP16_>(d1[d] * s1, h, l);
-            const uint32_t o = kmaj(row, c, CFG::SBO);
-            *reinterpret_cast<uint16_t*>(a_hi + o) = h;
-            *reinterpret_cast<uint16_t*>(a_lo + o) = l;
-            split16<CFG::FP16_>(d1[R + d] * s1, h, l);
-            const uint32_t o2 = kmaj(row, R + c, CFG::SBO);
-            *reinterpret_cast<uint16_t*>(a_hi + o2) = h;
-            *reinterpret_cast<uint16_t*>(a_lo + o2) = l;
+            t_re[(bl * R + d) * (R + 1) + c] = d1[d];
+            t_im[(bl * R + d) * (R + 1) + c] = d1[R + d];
         }
+        __syncthreads();
+        // row (b, d) = tid: the rotated values over c
+#pragma unroll
+        for (int cc = 0; cc < R; ++cc) {
+            d1[cc] = t_re[tid * (R + 1) + cc];
+            d1[R + cc] = t_im[tid * (R + 1) + cc];
+        }
+        const int e1 = block_exponent<R>(d1);
+        const float s1 = ldexpf(1.f, -e1);
+        __syncthreads();     // transpose reads done before the operand overwrites it
+#pragma unroll
+        for (int k8 = 0; k8 < 2 * R / 8; ++k8)
+            store_row8<CFG::FP16_>(a_hi, a_lo, kmaj(tid, 8 * k8, CFG::SBO), d1 + 8 * k8, s1);
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
             issue_gemm<CFG>(tbase + NM, sa_hi, sa_lo, sb_hi, sb_lo);
-            tc::mma_commit(mb0);
+            tc::mma_commit(mb_mma);
         }
-        if (__syncthreads_or(!tc::mbar_wait(mb0, phase))) { bad = 1; break; }
-        phase ^= 1;
+        if (__syncthreads_or(!tc::mbar_wait(mb_mma, ph_mma))) { bad = 1; break; }
+        ph_mma ^= 1;
         tc::fence_after_sync();
-        // ---- row (b, d): y[d + R * k2] for every k2, scales undone
+        // ---- row (b, d): y[d + R * k2] for every k2, scales undone, via a
+        // shared output tile and one bulk store per plane
         float d2[2 * R];
         tmem_row<R>(lane_base + NM, d2);
         tc::fence_before_sync();
         const float us = ldexpf(1.f, e0 + e1);
-        if (active) {
 #pragma unroll
-            for (int k2 = 0; k2 < R; ++k2) {
-                yr[base + c + R * k2] = d2[k2] * us;
-                yi[base + c + R * k2] = d2[R + k2] * us;
-            }
+        for (int k2 = 0; k2 < R; ++k2) {
+            y_re[bl * N + c + R * k2] = d2[k2] * us;
+            y_im[bl * N + c + R * k2] = d2[R + k2] * us;
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)(cnt * N * 4);
+            tc::bulk_s2g(yr + first * N, tc::smem_u32(y_re), bytes);
+            tc::bulk_s2g(yi + first * N, tc::smem_u32(y_im), bytes);
+            tc::bulk_commit();
         }
     }
-    if (bad && tid == 0) atomicExch(status, SDFT_ERR_TIMEOUT);
+    if (tid == 0) {
+        tc::bulk_wait0();                          // output stores complete
+        if (x_pending) tc::mbar_wait(mb_x, ph_x);  // no input copy left in flight (bounded)
+        if (bad) atomicExch(status, SDFT_ERR_TIMEOUT);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
