@@ -533,6 +533,10 @@ def run_workload(args) -> None:
         n = args.n
         batch = args.batch or max(1, (1 << 26) // n)
         xr_h, xi_h = workloads.normal_planes(n, batch, seed=1)
+        if args.schedule is not None:
+            from paper_2504_07264_gb300 import sdft as S
+            if S.sdft_schedule_select(n, args.dtype, args.schedule) != S.SDFT_OK:
+                raise SystemExit(f"no schedule {args.schedule} for N={n} dtype {args.dtype}")
         line.update(_measure_uniform(n, batch, xr_h, xi_h, args.steps, args.warmup, stream,
                                      dtype=args.dtype))
         line["metric"] = f"planar DFT Gpts/s, N={n} B={batch} dtype {args.dtype}"
@@ -571,6 +575,8 @@ def main(argv=None) -> int:
     ap.add_argument("--n", type=int, default=1024, help="length for --workload uniform")
     ap.add_argument("--dtype", type=int, default=0,
                     help="arithmetic path for --workload uniform (0 FP32, 1 split-BF16, 2 split-FP16)")
+    ap.add_argument("--schedule", type=int, default=None,
+                    help="compiled schedule index for --workload uniform (default: the tuned one)")
     ap.add_argument("--batch", type=int, default=None,
                     help="transforms per step (default: the workload's own batch, 65536 for "
                          "the headline; smaller only for profiling captures)")

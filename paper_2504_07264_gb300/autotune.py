@@ -71,7 +71,7 @@ def tune_one(n: int, dtype: int = S.SDFT_F32, points: int = 1 << 26, reps: int =
         raise S.SdftError(-best, f"sdft_autotune({n})")
     times = [float(v) for v in ms]
     best = pick(times)
-    S.sdft_schedule_select(n, dtype, best)
+    S.lib().sdft_schedule_select(n, dtype, best)
     return {"index": int(best), "ms": times, "batch": batch,
             "schedules": [S.sdft_schedule_describe(n, dtype, i) for i in range(count)]}
 
@@ -98,7 +98,7 @@ def apply(table: dict, name: str | None = None) -> int:
         for n, rec in per_n.items():
             idx = int(rec["index"])
             if idx < S.sdft_schedule_count(int(n), int(dtype)) and \
-                    S.sdft_schedule_select(int(n), int(dtype), idx) == S.SDFT_OK:
+                    S.lib().sdft_schedule_select(int(n), int(dtype), idx) == S.SDFT_OK:
                 applied += 1
     return applied
 

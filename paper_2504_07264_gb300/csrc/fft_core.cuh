@@ -212,16 +212,23 @@ __device__ __forceinline__ void step_gather(float (&re)[S::E], float (&im)[S::E]
         }
 }
 
-template <class S, int s, bool ADJ, class TW, class XW, class ST>
-__device__ __forceinline__ void step_compute_scatter(float (&re)[S::E], float (&im)[S::E],
-                                                     const int t, const W64& w, TW& tw, XW& xw,
-                                                     ST& st) {
+// The register DFTs of step s (no memory access).
+template <class S, int s, bool ADJ>
+__device__ __forceinline__ void step_compute(float (&re)[S::E], float (&im)[S::E], const W64& w) {
     using K = StepK<S, s>;
 #pragma unroll
     for (int f = 0; f < K::F; ++f) {
         if constexpr (S::DIT) dft_regs_dit<K::R, ADJ>(re, im, f * K::R, w);
         else dft_regs<K::R, ADJ>(re, im, f * K::R, w);
     }
+}
+
+// The rotations and exchange writes (or, for the last step, output stores)
+// of step s.
+template <class S, int s, bool ADJ, class TW, class XW, class ST>
+__device__ __forceinline__ void step_scatter(float (&re)[S::E], float (&im)[S::E], const int t,
+                                             TW& tw, XW& xw, ST& st) {
+    using K = StepK<S, s>;
 #pragma unroll
     for (int f = 0; f < K::F; ++f) {
         const int c = t + S::T * f;
@@ -238,6 +245,14 @@ __device__ __forceinline__ void step_compute_scatter(float (&re)[S::E], float (&
             }
         }
     }
+}
+
+template <class S, int s, bool ADJ, class TW, class XW, class ST>
+__device__ __forceinline__ void step_compute_scatter(float (&re)[S::E], float (&im)[S::E],
+                                                     const int t, const W64& w, TW& tw, XW& xw,
+                                                     ST& st) {
+    step_compute<S, s, ADJ>(re, im, w);
+    step_scatter<S, s, ADJ>(re, im, t, tw, xw, st);
 }
 
 // Run all steps of S.  `sync` separates exchange writes from reads (and the

@@ -45,14 +45,17 @@ struct KernelInfo {
     int64_t scratch_per_cta;     // float2 scratch entries per resident CTA (0 = none)
     int launches;                // kernel launches per call
     bool queue;                  // run as items of the persistent work-queue kernel
+    int cluster;                 // CTAs per thread-block cluster (0: no clusters)
     cudaError_t (*prepare)();    // one-time function attributes
     int (*blocks_per_sm)();      // occupancy of the kernel
+    int (*resident_ctas)();      // cluster kernels: CTAs resident over the GPU (else null)
     cudaError_t (*launch)(const LaunchArgs&);
 };
 
 // Tables of compiled configurations (defined by the kernel units).
 const KernelInfo* rows_kernel(int logn);      // N = 2 .. 16384, one kernel
 const KernelInfo* large_kernel(int logn);     // N = 32768, 65536
+const KernelInfo* cluster_kernel(int logn, int idx);   // N = 16384 .. 65536, one cluster per transform
 
 // Twiddle generation (twiddle.cu): fill `count` descriptors into `dst`
 // (device), and the 64-entry register constant table into `w64`.

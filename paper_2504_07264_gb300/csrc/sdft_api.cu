@@ -59,11 +59,13 @@ const KernelInfo* f32_candidate(int logn, int idx) {
         if (k) return k;
         int n = 0;
         while (rows_candidate_big(logn, n)) ++n;
-        return idx == n ? queue_candidate(14) : nullptr;
+        if (idx == n) return queue_candidate(14);
+        return idx > n ? cluster_kernel(14, idx - n - 1) : nullptr;
     }
     if (logn >= 15 && logn <= 16) {
         if (idx == 0) return queue_candidate(logn);
         if (idx == 1) return large_kernel(logn);
+        if (idx >= 2) return cluster_kernel(logn, idx - 2);
     }
     return nullptr;
 }
@@ -251,7 +253,9 @@ int launch(const sdft_plan* p, int direction, const float* xr, const float* xi, 
     a.grid = p->grid;
     a.stream = stream;
     a.adj = (direction == SDFT_ADJOINT);
-    const long long tiles = (batch + p->kern->transforms_per_cta - 1) / p->kern->transforms_per_cta;
+    // CTAs that have work: one per tile, or a whole cluster per transform
+    const long long tiles = (batch + p->kern->transforms_per_cta - 1) /
+                            p->kern->transforms_per_cta * std::max(1, p->kern->cluster);
     if (scratch == nullptr && tiles < a.grid) a.grid = (int)std::max<long long>(tiles, 1);
     return p->kern->launch(a) == cudaSuccess ? SDFT_OK : SDFT_ERR_CUDA;
 }
@@ -573,6 +577,10 @@ sdft_plan* plan_create_idx(int64_t n, int64_t batch, int dtype, int idx) {
         p->occupancy = k->blocks_per_sm();
         const int bps = std::max(1, p->occupancy);
         p->grid = bps * sms;
+        if (k->resident_ctas) {              // cluster kernels: whole clusters only
+            p->grid = k->resident_ctas();
+            if (p->grid < std::max(1, k->cluster)) { status = SDFT_ERR_CUDA; break; }
+        }
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             status = SDFT_ERR_CUDA; break;
         }

@@ -157,6 +157,11 @@ def sdft_schedule_describe(n: int, dtype: int, index: int) -> str:
 
 
 def sdft_schedule_select(n: int, dtype: int, index: int) -> int:
+    """Select compiled schedule `index` for later plans of (n, dtype).  The
+    tuning table is applied first, so an explicit choice is never replaced
+    by it afterwards."""
+    from . import autotune
+    autotune.ensure_applied()
     return lib().sdft_schedule_select(n, dtype, index)
 
 

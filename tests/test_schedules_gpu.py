@@ -61,3 +61,38 @@ def test_autotune_picks_a_schedule():
         assert S.sdft_schedule_selected(4096, 0) == rec["index"]
     finally:
         S.sdft_schedule_select(4096, 0, prev)
+
+
+def _cluster_indices(n):
+    from paper_2504_07264_gb300 import build
+    from paper_2504_07264_gb300 import sdft as S
+    build.build()
+    return [i for i in range(S.sdft_schedule_count(n, 0))
+            if "cluster of" in S.sdft_schedule_describe(n, 0, i)]
+
+
+@pytest.mark.parametrize("logn,idx", [(m, i) for m in (14, 15, 16) for i in _cluster_indices(1 << m)])
+def test_cluster_kernel_persistent_loop(logn, idx):
+    """The cluster kernels with more transforms than resident clusters: every
+    cluster runs several transforms, and the last one is ragged against the
+    grid.  All transforms are checked against the oracle, both directions,
+    and the second direction runs in place."""
+    from paper_2504_07264_gb300 import Plan
+    from paper_2504_07264_gb300 import sdft as S
+    n = 1 << logn
+    prev = S.sdft_schedule_selected(n, 0)
+    try:
+        assert S.sdft_schedule_select(n, 0, idx) == S.SDFT_OK
+        with Plan(n, 1) as probe:
+            clusters = probe.grid // (n // 8192)
+        batch = 2 * clusters + 3
+        xr, xi = W.normal_planes(n, batch, seed=950 + logn)
+        with Plan(n, batch) as plan:
+            assert "cluster of" in plan.describe()
+            yr, yi = gpu_run(xr, xi, 0, plan=plan)
+            assert rel_l2_rows(yr, yi, *O.dft_factored_dit(xr, xi)).max() <= TOL_F32
+            zr, zi = gpu_run(xr, xi, 1, plan=plan, inplace=True)
+            assert rel_l2_rows(zr, zi, *O.adjoint_factored(xr, xi)).max() <= TOL_F32
+            assert plan.sync_status() == S.SDFT_OK
+    finally:
+        S.sdft_schedule_select(n, 0, prev)
