@@ -87,8 +87,16 @@ struct ClusterCfg {
     static constexpr int WORK_FLOATS = 2 * A * CQ;
     static_assert(2 * C * AQ == WORK_FLOATS, "the passes use equal buffers");
     static constexpr size_t SMEM = (size_t)WORK_FLOATS * sizeof(float);
-    // twiddle tables: A-DFT step 0, C-DFT step 0, then W_N^{col * d} at [d][col]
-    static constexpr int64_t TWA = 0, TWC = A, TWB = A + C, TW_TOTAL = A + C + (int64_t)N;
+    // The pass-1 rotation W_N^{col * k}, k = lo + P * d (P = the first A-step
+    // radix, lo < P, d < R1 = the second), is taken as the product
+    // W_N^{col * lo} * W_{N/P}^{col * d} of two small tables: a CTA's slices
+    // of them (P + R1 rows of its CQ columns) stay in L1, where a full
+    // [A][C] table would not.
+    static constexpr int P = 1 << SA::lr(0), R1 = 1 << SA::lr(1);
+    // twiddle tables: A-DFT step 0, C-DFT step 0, W_N^{col lo} at [lo][col],
+    // W_{N/P}^{col d} at [d][col]
+    static constexpr int64_t TWA = 0, TWC = A, TWB1 = A + C, TWB2 = TWB1 + (int64_t)P * C;
+    static constexpr int64_t TW_TOTAL = TWB2 + (int64_t)R1 * C;
 };
 
 // Pass 1 from `ld` (step-0 source), Y into `work`.  Its first barrier orders
@@ -114,19 +122,41 @@ __device__ __forceinline__ void pass1(LD ld, float* const work, const int tid,
     auto twf = [&](int, int dd, int nl) -> float2 {
         return __ldg(tw + CFG::TWA + dd * (A >> SA::lr(0)) + nl);
     };
-    auto st = [&](int k, float r, float i) {
-        rot<ADJ>(r, i, __ldg(tw + CFG::TWB + (int64_t)k * C + col));
-        y_re[sub1 * A + (k ^ (sub1 & 31))] = r;
-        y_im[sub1 * A + (k ^ (sub1 & 31))] = i;
-    };
+    auto none = [](int, float, float) {};
     float re[SA::E], im[SA::E];
     step_gather<SA, 0, ADJ>(re, im, ta, ld, xrd);
     __syncthreads();
-    step_compute_scatter<SA, 0, ADJ>(re, im, ta, w, twf, xw, st);
+    step_compute_scatter<SA, 0, ADJ>(re, im, ta, w, twf, xw, none);
     __syncthreads();
     step_gather<SA, 1, ADJ>(re, im, ta, ld, xrd);
     __syncthreads();   // exchange reads done before Y (same memory) is written
-    step_compute_scatter<SA, 1, ADJ>(re, im, ta, w, twf, xw, st);
+    // last step: register DFTs, then output k = lo + P * d rotated by
+    // W_N^{col k} = W_N^{col lo} * W_{N/P}^{col d} and written to Y
+    using K = StepK<SA, 1>;
+    static_assert(K::P == CFG::P && K::R == CFG::R1 && K::LAST, "two-step A-DFT");
+    step_compute<SA, 1, ADJ>(re, im, w);
+    float2 fac[K::R];
+#pragma unroll
+    for (int dd = 1; dd < K::R; ++dd) fac[dd] = __ldg(tw + CFG::TWB2 + dd * C + col);
+#pragma unroll
+    for (int f = 0; f < K::F; ++f) {
+        const int lo = ta + SA::T * f;          // < P: the last step has no nl digit
+        const float2 base = __ldg(tw + CFG::TWB1 + lo * C + col);
+#pragma unroll
+        for (int dd = 0; dd < K::R; ++dd) {
+            const int reg = f * K::R + (SA::DIT ? dd : brevc(dd, K::LR));
+            const int k = lo + K::P * dd;
+            float2 wv = base;
+            if (dd != 0) {
+                wv.x = base.x * fac[dd].x - base.y * fac[dd].y;
+                wv.y = base.x * fac[dd].y + base.y * fac[dd].x;
+            }
+            float r = re[reg], i = im[reg];
+            rot<ADJ>(r, i, wv);
+            y_re[sub1 * A + (k ^ (sub1 & 31))] = r;
+            y_im[sub1 * A + (k ^ (sub1 & 31))] = i;
+        }
+    }
 }
 
 // Pass 2: rows of Y from every CTA of the cluster, results to `st`.  Every
@@ -276,10 +306,11 @@ KernelInfo cluster_info(const char* name) {
     k.smem = CFG::SMEM;
     k.transforms_per_cta = 1;
     k.cluster = CFG::Q;
-    k.ntables = 3;
+    k.ntables = 4;
     k.tables[0] = TableDesc{CFG::A, (int64_t)1 << SA::lr(0), (int64_t)CFG::A >> SA::lr(0), CFG::TWA};
     k.tables[1] = TableDesc{CFG::C, (int64_t)1 << SC::lr(0), (int64_t)CFG::C >> SC::lr(0), CFG::TWC};
-    k.tables[2] = TableDesc{CFG::N, CFG::A, CFG::C, CFG::TWB};
+    k.tables[2] = TableDesc{CFG::N, CFG::P, CFG::C, CFG::TWB1};
+    k.tables[3] = TableDesc{CFG::N / CFG::P, CFG::R1, CFG::C, CFG::TWB2};
     k.tw_entries = CFG::TW_TOTAL;
     k.scratch_per_cta = 0;
     k.launches = 1;
