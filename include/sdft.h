@@ -44,9 +44,9 @@
  *
  * Thread safety: a plan is immutable after creation; concurrent calls on one
  * plan from several host threads or streams are safe, with two exceptions:
- * plans of N >= 32768 own one scratch area that every call uses, so their
- * calls must be ordered on one stream; and the *_host calls share the plan's
- * staging buffers, so they must be serialised.
+ * plans on the two-pass CTA schedule of N >= 32768 own one scratch area that
+ * every call uses, so their calls must be ordered on one stream; and the
+ * *_host calls share the plan's staging buffers, so they must be serialised.
  */
 #ifndef SDFT_H_
 #define SDFT_H_
@@ -97,7 +97,10 @@ SDFT_API sdft_plan* sdft_plan_create(int64_t n, int64_t batch, int dtype);
  * lengths[0..count-1] (host array, read during the call only) are each a
  * power of two in [4, 65536].  Rows are concatenated in the order given.
  * Forward and adjoint calls on such a plan run as one persistent kernel
- * launch that claims transforms, largest first, from a device work queue.
+ * launch (thread-block clusters of 8 CTAs, replayed from a CUDA graph) that
+ * claims work from a device queue, largest transforms first: a transform of
+ * N >= 16384 is held in the shared memory of N / 8192 CTAs of a cluster,
+ * shorter ones run as tiles of one CTA.
  * Returns NULL on error (see sdft_last_error). */
 SDFT_API sdft_plan* sdft_plan_create_ragged(const int64_t* lengths, int64_t count, int dtype);
 
@@ -141,25 +144,27 @@ SDFT_API int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, 
 SDFT_API int sdft_plan_set_host_mode(sdft_plan* plan, int mode);
 
 /* Launch grid (CTAs) of a uniform plan's kernel.  The default is the
- * kernel's occupancy times the SM count; a persistent grid-stride loop makes
- * any grid >= 1 correct.  Plans whose kernel owns per-CTA scratch (N >= 32768)
- * and ragged plans keep their grid: SDFT_ERR_INVALID_ARG. */
+ * kernel's occupancy times the SM count (for cluster kernels: the clusters
+ * that fit at once, times their size); a persistent grid-stride loop makes
+ * any grid >= 1 correct (cluster kernels round it down to whole clusters, at
+ * least one).  Plans whose kernel owns per-CTA scratch and work-queue plans
+ * keep their grid: SDFT_ERR_INVALID_ARG. */
 SDFT_API int sdft_plan_set_grid(sdft_plan* plan, int grid);
 SDFT_API int sdft_plan_grid(const sdft_plan* plan);
 
-/* Work-queue plans (ragged plans, and uniform plans of N >= 16384 on their
- * default schedule) run long transforms as items that wait, on the device, for
- * the items they depend on.  Every such wait polls at most `polls` times
- * (~128 ns each; default 2^23, about a second); past that the kernel records
- * SDFT_ERR_TIMEOUT in the status word, stops waiting anywhere, finishes its
- * queue and exits (the results of that call are then invalid).  The status
- * stays set, and later calls skip their waits too, until
- * sdft_plan_sync_status reads and clears it.
+/* Bound of the device-side waits of a work-queue plan (ragged plans, and
+ * uniform plans on a work-queue schedule).  Their kernel needs no waits to
+ * compute; the only ones are those added by the testing hook below.  Every
+ * such wait polls at most `polls` times (~128 ns each; default 2^23, about a
+ * second); past that the kernel records SDFT_ERR_TIMEOUT in the status word,
+ * stops waiting anywhere and carries on.  The status stays set, and later
+ * calls skip their waits too, until sdft_plan_sync_status reads and clears it.
  * SDFT_ERR_INVALID_ARG for other plans or polls < 1. */
 SDFT_API int sdft_plan_set_wait_limit(sdft_plan* plan, int polls);
-/* Testing hook: make every pass-2 dependency of a work-queue plan with long
- * transforms unreachable (on != 0) or normal again (on == 0), so that the
- * bounded-wait path can be exercised without any fault on the GPU. */
+/* Testing hook: make every long-transform item (N >= 16384) of a work-queue
+ * plan first wait for a device word that nothing sets (on != 0), or not
+ * (on == 0), so that the bounded-wait path can be exercised without any
+ * fault on the GPU.  SDFT_ERR_INVALID_ARG for plans without long transforms. */
 SDFT_API int sdft_plan_inject_unreachable_wait(sdft_plan* plan, int on);
 
 /* Wait for `stream`, then read and clear the plan's device status word:

@@ -1,203 +1,13 @@
-// cluster.cu -- long transforms (N = 16384 .. 65536) held in the distributed
-// shared memory of a thread-block cluster.
-//
-// N = A * C, n = col + C * ntop, k = d + A * k2 (the regrouping of the radix-2
-// factors of Eq. (6) used throughout the library):
-//   pass 1: for every column col, the A-point DFT over ntop, rotated by
-//           W_N^{col * d}                                 -> Y[d][col]
-//   pass 2: for every row d, the C-point DFT over col     -> y[d + A * k2]
-// One transform is owned by a cluster of Q CTAs.  CTA q of the cluster runs
-// pass 1 on columns [q C/Q, (q+1) C/Q) and keeps its part of Y in its own
-// shared memory; after a cluster barrier it runs pass 2 on rows
-// [q A/Q, (q+1) A/Q), reading each row's C values from the shared memory of
-// all Q CTAs (ld.shared::cluster).  The intermediate never leaves the chip:
-// HBM sees one read and one write of every point, as for short transforms.
-// Each CTA holds N/Q = 8192 points.  The grid is persistent: cluster c handles
-// transforms c, c + (clusters), ...
-//
-// Y is stored column-major, Y[c][d] at c * A + (d ^ (c mod 32)): in pass 1 a
-// warp (32 columns, one d) writes 32 different banks, and in pass 2 a warp
-// (32 consecutive rows d, one column) reads one whole 128-byte line of a
-// remote CTA's shared memory per load.  Remote loads whose lanes touch
-// different lines are split into one network transaction per line.
-//
-// Ordering: a second cluster barrier, split into arrive (after this CTA's
-// remote reads) and wait (before this CTA overwrites Y), lets the pass-2 step-0
-// register DFTs run while the barrier completes.  No CTA leaves the kernel
-// before every remote read of its shared memory has finished (the last wait).
-//
-// Each CTA runs 256 threads x 32 values; two CTAs (of different clusters)
-// share an SM.  Pass 1 loads straight into registers and pass 2 stores
-// straight from registers.
-#include "fft_core.cuh"
+// cluster.cu -- the uniform cluster kernel for N = 16384 .. 65536: one
+// thread-block cluster of N / 8192 CTAs per transform (kernels_cluster.cuh),
+// two CTAs (of different clusters) per SM, a persistent grid: cluster c
+// handles transforms c, c + (clusters), ...  Pass 1 loads straight into
+// registers and pass 2 stores straight from registers.
+#include "kernels_cluster.cuh"
 #include "launch.h"
 
 namespace sdft {
 namespace {
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t cluster_id() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t cluster_count() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_arrive() {
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// the address of the same shared-memory location in CTA `rank` of the cluster
-__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ float ld_cluster(uint32_t addr) {
-    float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr));
-    return v;
-}
-
-template <int LOGA, int LOGC, int LOGQ, class SA, class SC>
-struct ClusterCfg {
-    using SA_ = SA;
-    using SC_ = SC;
-    static constexpr int THREADS = 256;
-    static constexpr int Q = 1 << LOGQ;
-    static constexpr int A = 1 << LOGA, C = 1 << LOGC, N = A * C, LOGN = LOGA + LOGC;
-    static constexpr int LOGCQ = LOGC - LOGQ, CQ = 1 << LOGCQ;   // pass-1 columns per CTA
-    static constexpr int AQ = A / Q;                              // pass-2 rows per CTA
-    static_assert(SA::N == A && SC::N == C, "sub-DFT sizes");
-    static_assert(SA::NS == 2 && SC::NS == 2, "two-step sub-DFTs");
-    static_assert(CQ * SA::T == THREADS && AQ * SC::T == THREADS, "one CTA per column / row tile");
-    static_assert(CQ >= 32 && AQ >= 32, "a warp covers 32 consecutive columns / rows");
-    static_assert(A % 32 == 0, "Y columns are whole 128-byte lines");
-    // one buffer for the pass-1 exchange [L][CQ], Y and the pass-2 exchange
-    // [L][AQ], each 2 * 8192 floats
-    static constexpr int WORK_FLOATS = 2 * A * CQ;
-    static_assert(2 * C * AQ == WORK_FLOATS, "the passes use equal buffers");
-    static constexpr size_t SMEM = (size_t)WORK_FLOATS * sizeof(float);
-    // The pass-1 rotation W_N^{col * k}, k = lo + P * d (P = the first A-step
-    // radix, lo < P, d < R1 = the second), is taken as the product
-    // W_N^{col * lo} * W_{N/P}^{col * d} of two small tables: a CTA's slices
-    // of them (P + R1 rows of its CQ columns) stay in L1, where a full
-    // [A][C] table would not.
-    static constexpr int P = 1 << SA::lr(0), R1 = 1 << SA::lr(1);
-    // twiddle tables: A-DFT step 0, C-DFT step 0, W_N^{col lo} at [lo][col],
-    // W_{N/P}^{col d} at [d][col]
-    static constexpr int64_t TWA = 0, TWC = A, TWB1 = A + C, TWB2 = TWB1 + (int64_t)P * C;
-    static constexpr int64_t TW_TOTAL = TWB2 + (int64_t)R1 * C;
-};
-
-// Pass 1 from `ld` (step-0 source), Y into `work`.  Its first barrier orders
-// the exchange writes after the previous transform's last reads of `work`.
-template <class CFG, bool ADJ, class LD>
-__device__ __forceinline__ void pass1(LD ld, float* const work, const int tid,
-                                      const int col, const float2* __restrict__ tw, const W64& w) {
-    using SA = typename CFG::SA_;
-    constexpr int A = CFG::A, C = CFG::C, CQ = CFG::CQ;
-    const int sub1 = tid % CQ, ta = tid / CQ;
-    float* const x_re = work;                 // exchange [L][sub1]
-    float* const x_im = work + A * CQ;
-    float* const y_re = work;                 // Y[c][dd], swizzled
-    float* const y_im = work + A * CQ;
-    auto xw = [&](int L, float r, float i) {
-        x_re[L * CQ + sub1] = r;
-        x_im[L * CQ + sub1] = i;
-    };
-    auto xrd = [&](int L, float& r, float& i) {
-        r = x_re[L * CQ + sub1];
-        i = x_im[L * CQ + sub1];
-    };
-    auto twf = [&](int, int dd, int nl) -> float2 {
-        return __ldg(tw + CFG::TWA + dd * (A >> SA::lr(0)) + nl);
-    };
-    auto none = [](int, float, float) {};
-    float re[SA::E], im[SA::E];
-    step_gather<SA, 0, ADJ>(re, im, ta, ld, xrd);
-    __syncthreads();
-    step_compute_scatter<SA, 0, ADJ>(re, im, ta, w, twf, xw, none);
-    __syncthreads();
-    step_gather<SA, 1, ADJ>(re, im, ta, ld, xrd);
-    __syncthreads();   // exchange reads done before Y (same memory) is written
-    // last step: register DFTs, then output k = lo + P * d rotated by
-    // W_N^{col k} = W_N^{col lo} * W_{N/P}^{col d} and written to Y
-    using K = StepK<SA, 1>;
-    static_assert(K::P == CFG::P && K::R == CFG::R1 && K::LAST, "two-step A-DFT");
-    step_compute<SA, 1, ADJ>(re, im, w);
-    float2 fac[K::R];
-#pragma unroll
-    for (int dd = 1; dd < K::R; ++dd) fac[dd] = __ldg(tw + CFG::TWB2 + dd * C + col);
-#pragma unroll
-    for (int f = 0; f < K::F; ++f) {
-        const int lo = ta + SA::T * f;          // < P: the last step has no nl digit
-        const float2 base = __ldg(tw + CFG::TWB1 + lo * C + col);
-#pragma unroll
-        for (int dd = 0; dd < K::R; ++dd) {
-            const int reg = f * K::R + (SA::DIT ? dd : brevc(dd, K::LR));
-            const int k = lo + K::P * dd;
-            float2 wv = base;
-            if (dd != 0) {
-                wv.x = base.x * fac[dd].x - base.y * fac[dd].y;
-                wv.y = base.x * fac[dd].y + base.y * fac[dd].x;
-            }
-            float r = re[reg], i = im[reg];
-            rot<ADJ>(r, i, wv);
-            y_re[sub1 * A + (k ^ (sub1 & 31))] = r;
-            y_im[sub1 * A + (k ^ (sub1 & 31))] = i;
-        }
-    }
-}
-
-// Pass 2: rows of Y from every CTA of the cluster, results to `st`.  Every
-// CTA's remote reads of this CTA's Y have finished when it returns.
-template <class CFG, bool ADJ, class ST>
-__device__ __forceinline__ void pass2(ST st, float* const work, const uint32_t y_sh, const int tid,
-                                      const int d, const float2* __restrict__ tw, const W64& w) {
-    using SC = typename CFG::SC_;
-    constexpr int A = CFG::A, C = CFG::C, CQ = CFG::CQ, AQ = CFG::AQ;
-    const int sub2 = tid % AQ, tc = tid / AQ;
-    float* const x_re = work;                 // exchange [L][sub2]
-    float* const x_im = work + C * AQ;
-    // column L of row d lives in CTA L / CQ at Y[L % CQ][d]
-    auto ld = [&](int L, float& r, float& i) {
-        const int c = L & (CQ - 1);
-        const uint32_t a = map_rank(y_sh + 4u * (uint32_t)(c * A + (d ^ (c & 31))),
-                                    (uint32_t)(L >> CFG::LOGCQ));
-        r = ld_cluster(a);
-        i = ld_cluster(a + 4u * (uint32_t)(A * CQ));
-    };
-    auto xw = [&](int L, float r, float i) {
-        x_re[L * AQ + sub2] = r;
-        x_im[L * AQ + sub2] = i;
-    };
-    auto xrd = [&](int L, float& r, float& i) {
-        r = x_re[L * AQ + sub2];
-        i = x_im[L * AQ + sub2];
-    };
-    auto twf = [&](int, int dd, int nl) -> float2 {
-        return __ldg(tw + CFG::TWC + dd * (C >> SC::lr(0)) + nl);
-    };
-    float re[SC::E], im[SC::E];
-    step_gather<SC, 0, ADJ>(re, im, tc, ld, xrd);
-    cluster_arrive();   // this CTA's remote reads are done
-    step_compute<SC, 0, ADJ>(re, im, w);
-    cluster_wait();     // every CTA's reads of Y are done: Y may be overwritten
-    step_scatter<SC, 0, ADJ>(re, im, tc, twf, xw, st);
-    __syncthreads();
-    step_gather<SC, 1, ADJ>(re, im, tc, ld, xrd);
-    step_compute_scatter<SC, 1, ADJ>(re, im, tc, w, twf, xw, st);
-}
 
 template <class CFG, bool ADJ>
 __global__ void __launch_bounds__(256, 2)
@@ -219,7 +29,7 @@ k_cluster(const float* __restrict__ xr, const float* __restrict__ xi, float* __r
             r = gxr[col + C * L];
             i = gxi[col + C * L];
         };
-        pass1<CFG, ADJ>(ld, work, tid, col, tw, w);
+        pass1<CFG, ADJ>(ld, [] {}, work, tid, col, tw, w);
         cluster_arrive();   // Y of this CTA complete (release) ...
         cluster_wait();     // ... and of every CTA of the cluster (acquire)
         float* const gyr = yr + t * CFG::N;
@@ -228,7 +38,7 @@ k_cluster(const float* __restrict__ xr, const float* __restrict__ xi, float* __r
             gyr[d + A * k2] = r;
             gyi[d + A * k2] = i;
         };
-        pass2<CFG, ADJ>(st, work, y_sh, tid, d, tw, w);
+        pass2<CFG, ADJ>(st, work, y_sh, tid, d, 0, tw, w);
     }
 }
 
@@ -324,13 +134,11 @@ KernelInfo cluster_info(const char* name) {
 }  // namespace
 
 const KernelInfo* cluster_kernel(int logn, int idx) {
-    using R256 = Steps<8, 5, 5, 3, 0>;   // 8 threads x 32 values, radix [32,8]
-    using R128 = Steps<7, 5, 5, 2, 0>;   // 4 threads x 32 values, radix [32,4]
-    static const KernelInfo k14 = cluster_info<ClusterCfg<7, 7, 1, R128, R128>>(
+    static const KernelInfo k14 = cluster_info<Cluster14>(
         "N=16384: cluster of 2 CTAs, distributed shared memory, 128 x 128, radix [32,4]x[32,4]");
-    static const KernelInfo k15 = cluster_info<ClusterCfg<8, 7, 2, R256, R128>>(
+    static const KernelInfo k15 = cluster_info<Cluster15>(
         "N=32768: cluster of 4 CTAs, distributed shared memory, 256 x 128, radix [32,8]x[32,4]");
-    static const KernelInfo k16 = cluster_info<ClusterCfg<8, 8, 3, R256, R256>>(
+    static const KernelInfo k16 = cluster_info<Cluster16>(
         "N=65536: cluster of 8 CTAs, distributed shared memory, 256 x 256, radix [32,8]x[32,8]");
     if (idx != 0) return nullptr;
     switch (logn) {

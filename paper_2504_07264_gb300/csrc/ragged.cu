@@ -1,22 +1,27 @@
 // ragged.cu -- one persistent launch for a batch of mixed power-of-two lengths.
 //
-// The plan turns the batch into a queue of work items, longest transforms
-// first.  Lengths up to 8192 are "row" items: 256 / T transforms of one
-// length processed by one 256-thread CTA with the row tile routine.  Lengths
-// 16384 .. 65536 are split into pass-1 and pass-2 items (kernels_items.cuh):
-// a pass-2 item waits until every pass-1 item of its transform has finished,
-// and the pass-1 items of a transform wait until the previous user of its
-// scratch slot (a ring of slots sized to stay in L2) has finished pass 2.
-// Every dependency points to an item earlier in the queue; the grid is
-// persistent (all CTAs resident at once) and CTAs claim items in queue order
-// with atomicAdd, so each awaited item is already running and the waits end.
-// Each wait is still bounded: past its limit the kernel records
-// SDFT_ERR_TIMEOUT in the plan's status word, every later wait returns at
-// once, and the kernel runs out its queue and exits.
-// The work counter and completion counters are zeroed by a memset node that
-// precedes the kernel in the plan's CUDA graph.
+// The kernel runs as thread-block clusters of 8 CTAs (256 threads each, two
+// per SM).  The plan turns the batch into a queue of cluster items, longest
+// transforms first, and each cluster claims one item at a time with an
+// atomicAdd by its first CTA, broadcast to the others through distributed
+// shared memory and a cluster barrier (each item claims the next one while
+// it runs; during a long item the claim rides on the item's own barriers):
+//   * a long item (N = 16384 .. 65536) is one, two or four transforms, each
+//     held by 8, 4 or 2 CTAs of the cluster in their shared memory and
+//     transformed in two passes with the exchange between them done by
+//     ld.shared::cluster (kernels_cluster.cuh) -- no global scratch, no
+//     inter-CTA waits;
+//   * a row item group (N <= 8192) is up to eight row items, one per CTA,
+//     each a tile of transforms of one length run by the row tile routine.
+// A transform is computed with the same arithmetic and tables as the uniform
+// kernel of its length (the cluster kernel for long lengths).
+// The work counter is zeroed by a memset node that precedes the kernel in the
+// plan's CUDA graph.  The kernel has no device-side waits of its own; for
+// tests, a plan can make every long item first wait for a word that nothing
+// sets, a wait bounded like all others: past its limit it records
+// SDFT_ERR_TIMEOUT in the status word and the item proceeds.
 #include "../../include/sdft.h"
-#include "kernels_items.cuh"
+#include "kernels_cluster.cuh"
 #include "kernels_rows.cuh"
 #include "ragged.h"
 
@@ -38,17 +43,12 @@ using R10 = RowCfg<10, 5, 5, 5, 0, 8>;
 using R11 = RowCfg<11, 5, 5, 4, 2, 4>;
 using R12 = RowCfg<12, 5, 5, 5, 2, 2>;
 using R13 = RowCfg<13, 5, 5, 5, 3, 1>;
-using S256 = Steps<8, 5, 5, 3, 0>;     // 8 threads x 32 values, radix [32,8]
-using S128 = Steps<7, 4, 4, 3, 0>;     // 8 threads x 16 values, radix [16,8]
-using I14 = ItemCfg<7, 7, S128, S128>;
-using I15 = ItemCfg<8, 7, S256, S128>;
-using I16 = ItemCfg<8, 8, S256, S256>;
 
 constexpr size_t smax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kSmem =
     smax(smax(smax(R6::SMEM, R7::SMEM), smax(R8::SMEM, R9::SMEM)),
          smax(smax(smax(R10::SMEM, R11::SMEM), smax(R12::SMEM, R13::SMEM)),
-              smax(I14::SMEM, smax(I15::SMEM, I16::SMEM))));
+              smax(Cluster14::SMEM, smax(Cluster15::SMEM, Cluster16::SMEM))));
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;
@@ -78,15 +78,6 @@ __device__ __forceinline__ bool cta_wait(const int* word, int target, const Ragg
     return ok;
 }
 
-// Publish one finished item: every thread's global writes, then the counter.
-__device__ __forceinline__ void cta_signal(int* word) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(word, 1);
-    }
-}
-
 template <class CFG, bool ADJ>
 __device__ __forceinline__ void ragged_rows(const RaggedArgs& a, const int4 item, float* smem) {
     using S = typename CFG::S;
@@ -101,66 +92,155 @@ __device__ __forceinline__ void ragged_rows(const RaggedArgs& a, const int4 item
                         a.tw[S::LOGN], a.w);
 }
 
-// item.y = long-transform index lt, item.z = tile, item.w = dependency
-// (pass 1: the long transform whose pass 2 must free the slot, or -1).
-template <class CFG, bool ADJ>
-__device__ __forceinline__ void ragged_pass1(const RaggedArgs& a, const int4 item, float* smem) {
-    const int lt = item.y;
-    if (item.w >= 0 && !cta_wait(a.done2 + item.w, a.tiles2[item.w], a)) return;
-    const long long row = a.long_offsets[lt];
-    float* const scr = reinterpret_cast<float*>(a.scratch + (size_t)a.long_slot[lt] * a.slot_size);
-    item_pass1<CFG, ADJ>(a.xr + row, a.xi + row, scr, scr + CFG::N, item.z, smem, a.tw[CFG::LOGN],
-                         a.w);
-    cta_signal(a.done1 + lt);
+// Work records.  The cluster's first thread claims a cluster item and writes
+// into every CTA's slot that CTA's share of it (st.shared::cluster), so no
+// CTA needs a dependent global load to start:
+//   x < 0                end of the queue
+//   x = kIdle            nothing for this CTA (row groups of fewer than 8)
+//   x = 2 .. 13          the row item itself (log2 N, first, count)
+//   x = kLong + log2 N   long item: y = 1 if this CTA holds a transform, whose
+//                        row start (floats) is z | w << 32
+// Two slots alternate, so a slot is rewritten only after every CTA has passed
+// a cluster barrier that follows its read.
+constexpr int kIdle = 1;
+
+__device__ __forceinline__ void st_cluster4(uint32_t addr, int4 v) {
+    asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};"
+                 :: "r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
 }
 
+__device__ __forceinline__ int4 load_citem(const RaggedArgs& a, int it) {
+    return it < a.nitems ? a.citems[it] : make_int4(-1, 0, 0, 0);
+}
+
+// Leader: the records of cluster item `ci` for every CTA, into `slot`.
+__device__ __forceinline__ void publish_work(const RaggedArgs& a, const int4 ci, int4* slot) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(slot);
+    int4 rec[kRaggedCluster];
+    if (ci.x < 0) {
+#pragma unroll
+        for (int r = 0; r < kRaggedCluster; ++r) rec[r] = make_int4(-1, 0, 0, 0);
+    } else if (ci.x >= kLong) {
+        const int lq = ci.x - kLong - 13;    // log2 of the CTAs per transform
+#pragma unroll
+        for (int r = 0; r < kRaggedCluster; ++r) {
+            const int sub = r >> lq;
+            if (sub < ci.z) {
+                const long long off = a.long_offsets[ci.y + sub];
+                rec[r] = make_int4(ci.x, 1, (int)(uint32_t)off, (int)(uint32_t)(off >> 32));
+            } else {
+                rec[r] = make_int4(ci.x, 0, 0, 0);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < kRaggedCluster; ++r)
+            rec[r] = r < ci.z ? a.items[ci.y + r] : make_int4(kIdle, 0, 0, 0);
+    }
+#pragma unroll
+    for (int r = 0; r < kRaggedCluster; ++r) st_cluster4(map_rank(s, (uint32_t)r), rec[r]);
+}
+
+// A long item: this CTA's share (rank q of the Q holding transform `sub`).
+// CTAs without a transform take the two cluster barriers only.  The
+// cluster's first thread claims the next item meanwhile and publishes its
+// records into `next` before the first barrier, so the next item starts
+// without a claim barrier of its own.
 template <class CFG, bool ADJ>
-__device__ __forceinline__ void ragged_pass2(const RaggedArgs& a, const int4 item, float* smem) {
-    const int lt = item.y;
-    if (!cta_wait(a.done1 + lt, CFG::TILES1 + a.dep_extra, a)) return;
-    const long long row = a.long_offsets[lt];
-    const float* scr =
-        reinterpret_cast<const float*>(a.scratch + (size_t)a.long_slot[lt] * a.slot_size);
-    item_pass2<CFG, ADJ>(scr, scr + CFG::N, a.yr + row, a.yi + row, item.z, smem,
-                         a.tw[CFG::LOGN], a.w);
-    cta_signal(a.done2 + lt);
+__device__ __forceinline__ void ragged_long(const RaggedArgs& a, const int4 rec, float* smem,
+                                            const uint32_t rank, int4* next) {
+    constexpr int Q = CFG::Q, A = CFG::A, C = CFG::C;
+    const int tid = (int)threadIdx.x;
+    const bool leader = rank == 0 && tid == 0;
+    const uint32_t sub = rank / Q, q = rank % Q;
+    int claim = 0;
+    if (leader) claim = atomicAdd(a.counter, 1);
+    if (a.inject) cta_wait(a.never, 1, a);
+    if (rec.y == 0) {         // never the leader's CTA: a long item holds >= 1 transform
+        cluster_arrive();     // the barrier after pass 1
+        cluster_wait();
+        cluster_arrive();     // the barrier inside pass 2
+        cluster_wait();
+        return;
+    }
+    const long long off = (long long)(((uint64_t)(uint32_t)rec.w << 32) | (uint32_t)rec.z);
+    const float2* tw = a.tw[CFG::LOGN];
+    const int col = (int)q * CFG::CQ + tid % CFG::CQ;
+    const int d = (int)q * CFG::AQ + tid % CFG::AQ;
+    const float* gxr = a.xr + off;
+    const float* gxi = a.xi + off;
+    auto ld = [&](int L, float& r, float& i) {
+        r = gxr[col + C * L];
+        i = gxi[col + C * L];
+    };
+    int4 nci = make_int4(-1, 0, 0, 0);
+    auto mid = [&] {
+        if (leader) nci = load_citem(a, claim);
+    };
+    pass1<CFG, ADJ>(ld, mid, smem, tid, col, tw, a.w);
+    if (leader) publish_work(a, nci, next);
+    cluster_arrive();
+    cluster_wait();
+    float* const gyr = a.yr + off;
+    float* const gyi = a.yi + off;
+    auto st = [&](int k2, float r, float i) {
+        gyr[d + A * k2] = r;
+        gyi[d + A * k2] = i;
+    };
+    pass2<CFG, ADJ>(st, smem, (uint32_t)__cvta_generic_to_shared(smem), tid, d, sub * Q, tw, a.w);
 }
 
 template <bool ADJ>
 __global__ void __launch_bounds__(kThreads, 2) k_ragged(const RaggedArgs a) {
     extern __shared__ float4 smem4[];
     float* const smem = reinterpret_cast<float*>(smem4);
-    __shared__ int s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();  // every thread has read s_item before it is claimed again
-        if (it >= a.nitems) break;
-        const int4 item = a.items[it];
-        switch (item.x) {
-            case 2: ragged_rows<R2, ADJ>(a, item, smem); break;
-            case 3: ragged_rows<R3, ADJ>(a, item, smem); break;
-            case 4: ragged_rows<R4, ADJ>(a, item, smem); break;
-            case 5: ragged_rows<R5, ADJ>(a, item, smem); break;
-            case 6: ragged_rows<R6, ADJ>(a, item, smem); break;
-            case 7: ragged_rows<R7, ADJ>(a, item, smem); break;
-            case 8: ragged_rows<R8, ADJ>(a, item, smem); break;
-            case 9: ragged_rows<R9, ADJ>(a, item, smem); break;
-            case 10: ragged_rows<R10, ADJ>(a, item, smem); break;
-            case 11: ragged_rows<R11, ADJ>(a, item, smem); break;
-            case 12: ragged_rows<R12, ADJ>(a, item, smem); break;
-            case 13: ragged_rows<R13, ADJ>(a, item, smem); break;
-            case kPass1 + 14: ragged_pass1<I14, ADJ>(a, item, smem); break;
-            case kPass1 + 15: ragged_pass1<I15, ADJ>(a, item, smem); break;
-            case kPass1 + 16: ragged_pass1<I16, ADJ>(a, item, smem); break;
-            case kPass2 + 14: ragged_pass2<I14, ADJ>(a, item, smem); break;
-            case kPass2 + 15: ragged_pass2<I15, ADJ>(a, item, smem); break;
-            case kPass2 + 16: ragged_pass2<I16, ADJ>(a, item, smem); break;
-            default: break;
+    __shared__ __align__(16) int4 s_work[2];
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0 && threadIdx.x == 0;
+    // every CTA of the cluster is running before any shared memory of it is
+    // written from another CTA; then the first item's records
+    cluster_arrive();
+    cluster_wait();
+    if (leader) publish_work(a, load_citem(a, atomicAdd(a.counter, 1)), &s_work[0]);
+    cluster_arrive();
+    cluster_wait();
+    // Each item publishes the records of the next one into the other slot
+    // before a cluster barrier: a long item before its own first barrier, a
+    // row group at its end, followed by a barrier that also lets the next
+    // item reuse every CTA's shared memory.
+    for (int par = 0;; par ^= 1) {
+        const int4 rec = s_work[par];
+        if (rec.x < 0) break;
+        int4* const next = &s_work[par ^ 1];
+        if (rec.x >= kLong) {
+            switch (rec.x - kLong) {
+                case 14: ragged_long<Cluster14, ADJ>(a, rec, smem, rank, next); break;
+                case 15: ragged_long<Cluster15, ADJ>(a, rec, smem, rank, next); break;
+                case 16: ragged_long<Cluster16, ADJ>(a, rec, smem, rank, next); break;
+                default: break;
+            }
+            continue;
         }
-        // the barrier at the loop top orders the next item's shared-memory
-        // writes after every thread's last read of this one
+        int claim = 0;
+        if (leader) claim = atomicAdd(a.counter, 1);
+        switch (rec.x) {
+            case 2: ragged_rows<R2, ADJ>(a, rec, smem); break;
+            case 3: ragged_rows<R3, ADJ>(a, rec, smem); break;
+            case 4: ragged_rows<R4, ADJ>(a, rec, smem); break;
+            case 5: ragged_rows<R5, ADJ>(a, rec, smem); break;
+            case 6: ragged_rows<R6, ADJ>(a, rec, smem); break;
+            case 7: ragged_rows<R7, ADJ>(a, rec, smem); break;
+            case 8: ragged_rows<R8, ADJ>(a, rec, smem); break;
+            case 9: ragged_rows<R9, ADJ>(a, rec, smem); break;
+            case 10: ragged_rows<R10, ADJ>(a, rec, smem); break;
+            case 11: ragged_rows<R11, ADJ>(a, rec, smem); break;
+            case 12: ragged_rows<R12, ADJ>(a, rec, smem); break;
+            case 13: ragged_rows<R13, ADJ>(a, rec, smem); break;
+            default: break;   // kIdle
+        }
+        if (leader) publish_work(a, load_citem(a, claim), next);
+        cluster_arrive();
+        cluster_wait();
     }
 }
 
@@ -171,7 +251,6 @@ RaggedClass row_class(int logn) {
     c.logn = logn;
     c.per_item = CFG::G;
     c.large = false;
-    c.tiles1 = c.tiles2 = 0;
     c.ntables = 0;
     if (S::NS > 1) {
         const int64_t n = S::N;
@@ -186,19 +265,18 @@ RaggedClass row_class(int logn) {
 }
 
 template <class CFG>
-RaggedClass item_class(int logn) {
+RaggedClass long_class(int logn) {
     using SA = typename CFG::SA_;
     using SC = typename CFG::SC_;
     RaggedClass c = {};
     c.logn = logn;
-    c.per_item = 1;
+    c.per_item = kRaggedCluster / CFG::Q;
     c.large = true;
-    c.tiles1 = CFG::TILES1;
-    c.tiles2 = CFG::TILES2;
-    c.ntables = 3;
+    c.ntables = 4;
     c.tables[0] = TableDesc{CFG::A, (int64_t)1 << SA::lr(0), (int64_t)CFG::A >> SA::lr(0), CFG::TWA};
     c.tables[1] = TableDesc{CFG::C, (int64_t)1 << SC::lr(0), (int64_t)CFG::C >> SC::lr(0), CFG::TWC};
-    c.tables[2] = TableDesc{CFG::N, CFG::A, CFG::C, CFG::TWB};
+    c.tables[2] = TableDesc{CFG::N, CFG::P, CFG::C, CFG::TWB1};
+    c.tables[3] = TableDesc{CFG::N / CFG::P, CFG::R1, CFG::C, CFG::TWB2};
     c.tw_entries = CFG::TW_TOTAL;
     return c;
 }
@@ -210,13 +288,13 @@ const RaggedClass* ragged_class(int logn) {
         RaggedClass{}, RaggedClass{}, row_class<R2>(2), row_class<R3>(3), row_class<R4>(4),
         row_class<R5>(5), row_class<R6>(6), row_class<R7>(7), row_class<R8>(8),
         row_class<R9>(9), row_class<R10>(10), row_class<R11>(11), row_class<R12>(12),
-        row_class<R13>(13), item_class<I14>(14), item_class<I15>(15), item_class<I16>(16)};
+        row_class<R13>(13), long_class<Cluster14>(14), long_class<Cluster15>(15),
+        long_class<Cluster16>(16)};
     return (logn >= 2 && logn <= 16) ? &c[logn] : nullptr;
 }
 
 int ragged_threads() { return kThreads; }
 size_t ragged_smem() { return kSmem; }
-int64_t ragged_slot_size() { return 65536; }
 
 const void* ragged_kernel_fn(bool adj) {
     return adj ? reinterpret_cast<const void*>(k_ragged<true>)
@@ -231,12 +309,25 @@ cudaError_t ragged_prepare() {
                                 (int)kSmem);
 }
 
-int ragged_blocks_per_sm() {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ragged<false>, kThreads, kSmem) !=
-        cudaSuccess)
+int ragged_resident_ctas() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
-    return n;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(kRaggedCluster * 2 * sms), 1, 1);
+    cfg.blockDim = dim3((unsigned)kThreads, 1, 1);
+    cfg.dynamicSmemBytes = kSmem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kRaggedCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_ragged<false>, &cfg) != cudaSuccess) return 0;
+    return clusters * kRaggedCluster;
 }
 
 }  // namespace sdft

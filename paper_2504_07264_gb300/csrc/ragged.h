@@ -6,10 +6,16 @@
 
 namespace sdft {
 
-// item.x: log2 N for row items; kPass1 + log2 N / kPass2 + log2 N for the two
-// passes of a long transform.
-constexpr int kPass1 = 100;
-constexpr int kPass2 = 200;
+// The kernel runs as thread-block clusters of kRaggedCluster CTAs.  A cluster
+// claims one cluster item at a time:
+//   x = log2 N (2 .. 13): a group of up to 8 row items; CTA r of the cluster
+//       runs row item y + r if r < z
+//   x = kLong + log2 N (14 .. 16): long transforms y .. y + z - 1 of the long
+//       list, one per N / 8192 CTAs of the cluster (z <= 8 * 8192 / N)
+// A row item (x = log2 N, y = first transform in the row order, z = count)
+// is `per_item` transforms of one length run by one CTA.
+constexpr int kLong = 100;
+constexpr int kRaggedCluster = 8;
 
 // Kernel arguments, passed by value.
 struct RaggedArgs {
@@ -18,20 +24,15 @@ struct RaggedArgs {
     float* yr;
     float* yi;
     const long long* offsets;       // row items: row start (floats) of each transform, in work order
-    const int4* items;              // (kind, first transform / long index, count / tile, dependency)
-    int nitems;
-    int* counter;                   // work counter, zero at launch
+    const int4* items;              // row items
+    const int4* citems;             // cluster items
+    int nitems;                     // cluster items
+    int* counter;                   // claimed cluster items (zero at launch)
     const long long* long_offsets;  // long transforms: row start (floats)
-    const int* long_slot;           // long transforms: scratch slot
-    const int* tiles2;              // long transforms: number of pass-2 items
-    int* done1;                     // long transforms: finished pass-1 items (zero at launch)
-    int* done2;                     // long transforms: finished pass-2 items (zero at launch)
+    int* never;                     // a word that stays zero (target of injected waits)
     int* status;                    // plan status word (SDFT_ERR_TIMEOUT on a wait that gave up)
     int wait_polls;                 // bound of every wait (polls of ~128 ns)
-    int dep_extra;                  // added to every pass-2 wait target (0; tests set 1 to
-                                    // make the dependency unreachable)
-    long long slot_size;            // float2 entries per scratch slot
-    float2* scratch;                // slots
+    int inject;                     // tests: every long item first waits for `never` to become 1
     const float2* tw[17];           // twiddle tables of each length class (by log2 N)
     W64 w;
 };
@@ -39,9 +40,8 @@ struct RaggedArgs {
 // One length class of the work-queue kernel.
 struct RaggedClass {
     int logn;
-    int per_item;               // transforms per row item (1 for long classes)
-    bool large;                 // split into pass-1 / pass-2 items
-    int tiles1, tiles2;         // items per pass of one long transform
+    int per_item;               // transforms per row item, or per cluster item (long classes)
+    bool large;                 // a long class: cluster items
     int ntables;
     TableDesc tables[4];
     int64_t tw_entries;
@@ -50,9 +50,8 @@ struct RaggedClass {
 const RaggedClass* ragged_class(int logn);   // log2 N in [2, 16], else null
 int ragged_threads();
 size_t ragged_smem();
-int64_t ragged_slot_size();                  // float2 entries per scratch slot
 const void* ragged_kernel_fn(bool adj);
 cudaError_t ragged_prepare();
-int ragged_blocks_per_sm();
+int ragged_resident_ctas();                  // whole clusters resident over the GPU
 
 }  // namespace sdft

@@ -31,9 +31,9 @@ const KernelInfo* queue_candidate(int logn) {
     static KernelInfo q[17];
     static const bool init = [] {
         static const char* names[17] = {};
-        names[14] = "N=16384: work-queue items, 128 x 128, 4 column + 4 row tiles per transform";
-        names[15] = "N=32768: work-queue items, 256 x 128, 4 column + 8 row tiles per transform";
-        names[16] = "N=65536: work-queue items, 256 x 256, 8 column + 8 row tiles per transform";
+        names[14] = "N=16384: work queue of cluster items, 4 transforms per cluster of 8 CTAs";
+        names[15] = "N=32768: work queue of cluster items, 2 transforms per cluster of 8 CTAs";
+        names[16] = "N=65536: work queue of cluster items, 1 transform per cluster of 8 CTAs";
         for (int l = 14; l <= 16; ++l) {
             q[l] = KernelInfo{};
             q[l].name = names[l];
@@ -103,16 +103,14 @@ struct RaggedState {
     bool uniform = false;             // a uniform batch of long transforms
     int64_t count = 0;
     long long* d_offsets = nullptr;
-    int4* d_items = nullptr;
-    int nitems = 0;
-    int nlong = 0;                     // long transforms (pass-1 / pass-2 items)
-    int slots = 0;                     // scratch slots in the ring
-    int* d_sync = nullptr;             // [work counter, done1[nlong], done2[nlong]]
+    int4* d_items = nullptr;           // row items
+    int4* d_citems = nullptr;          // cluster items
+    int nitems = 0;                    // cluster items
+    int nlong = 0;                     // long transforms
+    int* d_sync = nullptr;             // [work counter, a word that stays zero]
     long long* d_long_offsets = nullptr;
-    int* d_long_slot = nullptr;
-    int* d_tiles2 = nullptr;
     int wait_polls = 1 << 23;          // ~1 s of 128 ns polls
-    int dep_extra = 0;                 // fault injection for tests (unreachable waits)
+    int inject = 0;                    // tests: long items wait for a word nothing sets
     const float2* tw[17] = {};
     unsigned classes = 0;              // bit l set: some transform has log2 N = l
     cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -198,10 +196,9 @@ void free_plan_memory(sdft_plan* p) {
     }
     if (r.d_offsets) cudaFree(r.d_offsets);
     if (r.d_items) cudaFree(r.d_items);
+    if (r.d_citems) cudaFree(r.d_citems);
     if (r.d_sync) cudaFree(r.d_sync);
     if (r.d_long_offsets) cudaFree(r.d_long_offsets);
-    if (r.d_long_slot) cudaFree(r.d_long_slot);
-    if (r.d_tiles2) cudaFree(r.d_tiles2);
 }
 
 bool ranges_overlap(const void* a, const void* b, size_t bytes) {
@@ -263,7 +260,7 @@ int launch(const sdft_plan* p, int direction, const float* xr, const float* xi, 
 // Ragged plans: launch the direction's graph, building it on first use and
 // re-pointing its kernel node when the data pointers change.
 int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr,
-                  float* yi, cudaStream_t stream, float2* scratch) {
+                  float* yi, cudaStream_t stream) {
     RaggedState& r = p->rag;
     const int d = direction == SDFT_ADJOINT ? 1 : 0;
     RaggedArgs a = {};
@@ -273,18 +270,14 @@ int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi,
     a.yi = yi;
     a.offsets = r.d_offsets;
     a.items = r.d_items;
+    a.citems = r.d_citems;
     a.nitems = r.nitems;
     a.counter = r.d_sync;
     a.long_offsets = r.d_long_offsets;
-    a.long_slot = r.d_long_slot;
-    a.tiles2 = r.d_tiles2;
-    a.done1 = r.d_sync + 1;
-    a.done2 = r.d_sync + 1 + r.nlong;
+    a.never = r.d_sync + 1;
     a.status = p->d_status;
     a.wait_polls = r.wait_polls;
-    a.dep_extra = r.dep_extra;
-    a.slot_size = ragged_slot_size();
-    a.scratch = scratch;
+    a.inject = r.inject;
     for (int l = 0; l < 17; ++l) a.tw[l] = r.tw[l];
     a.w = p->w64;
     void* kargs[] = {&a};
@@ -302,12 +295,18 @@ int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi,
         mp.dst = r.d_sync;
         mp.value = 0;
         mp.elementSize = sizeof(int);
-        mp.width = (size_t)(1 + 2 * r.nlong);
+        mp.width = 2;
         mp.height = 1;
         mp.pitch = 0;
         cudaGraphNode_t mnode = nullptr;
+        cudaKernelNodeAttrValue cl = {};
+        cl.clusterDim.x = kRaggedCluster;
+        cl.clusterDim.y = 1;
+        cl.clusterDim.z = 1;
         if (cudaGraphAddMemsetNode(&mnode, r.graph[d], nullptr, 0, &mp) != cudaSuccess ||
             cudaGraphAddKernelNode(&r.knode[d], r.graph[d], &mnode, 1, &kp) != cudaSuccess ||
+            cudaGraphKernelNodeSetAttribute(r.knode[d], cudaKernelNodeAttributeClusterDimension,
+                                            &cl) != cudaSuccess ||
             cudaGraphInstantiate(&r.exec[d], r.graph[d], 0) != cudaSuccess) {
             if (r.graph[d]) cudaGraphDestroy(r.graph[d]);
             r.graph[d] = nullptr;
@@ -336,18 +335,16 @@ const void* mapped_host(const void* p) {
 
 int run(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr, float* yi,
         cudaStream_t stream, long long batch, float2* scratch) {
-    if (p->rag.on) return launch_ragged(p, direction, xr, xi, yr, yi, stream, scratch);
+    if (p->rag.on) return launch_ragged(p, direction, xr, xi, yr, yi, stream);
     return launch(p, direction, xr, xi, yr, yi, stream, batch, scratch);
 }
 
 // Ragged plans, and uniform plans of long transforms: build the work queue
-// of the persistent kernel (ragged.cu).  Long transforms (N >= 16384) come
-// first, their pass-1 items interleaved with the pass-2 items of the
-// transform `lag` places earlier; scratch slots are reused round-robin, the
-// pass-1 items of a transform depending on the pass 2 of the slot's previous
-// user (always earlier in the queue).  Row items follow, longest first.
+// of the persistent cluster kernel (ragged.cu).  Long transforms (N >= 16384)
+// come first, longest first, grouped into cluster items of 8 * 8192 points
+// (one, two or four transforms); then the row items, longest first, grouped
+// eight to a cluster item.
 sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform) {
-    constexpr int kMaxSlots = 48;         // 48 x 512 KiB = 24 MiB of scratch, L2-resident
     std::vector<int> logn((size_t)count);
     int64_t total = 0;
     for (int64_t t = 0; t < count; ++t) {
@@ -361,44 +358,25 @@ sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform
         for (int64_t t = 0; t < count; ++t) { start[(size_t)t] = o; o += lengths[t]; }
     }
     unsigned classes = 0;
+    std::vector<int4> citems;
     // long transforms, longest first
     std::vector<long long> long_off;
-    std::vector<int> long_logn;
     for (int l = kMaxLogN; l >= 2; --l) {
         const RaggedClass* c = ragged_class(l);
         if (!c->large) continue;
+        const int first = (int)long_off.size();
         for (int64_t t = 0; t < count; ++t)
-            if (logn[(size_t)t] == l) {
-                long_off.push_back(start[(size_t)t]);
-                long_logn.push_back(l);
-                classes |= 1u << l;
-            }
+            if (logn[(size_t)t] == l) long_off.push_back(start[(size_t)t]);
+        const int n_in = (int)long_off.size() - first;
+        if (n_in == 0) continue;
+        classes |= 1u << l;
+        for (int s0 = 0; s0 < n_in; s0 += c->per_item)
+            citems.push_back(make_int4(kLong + l, first + s0, std::min(c->per_item, n_in - s0), 0));
     }
     const int nlong = (int)long_off.size();
-    const int slots = std::min(nlong, kMaxSlots);
-    const int lag = std::max(1, slots / 2);
-    std::vector<int4> items;
-    std::vector<int> long_slot((size_t)nlong), tiles2((size_t)nlong);
-    for (int lt = 0; lt < nlong; ++lt) {
-        long_slot[(size_t)lt] = lt % std::max(slots, 1);
-        tiles2[(size_t)lt] = ragged_class(long_logn[(size_t)lt])->tiles2;
-    }
-    for (int k = 0; k < nlong + lag; ++k) {
-        if (k < nlong) {
-            const RaggedClass* c = ragged_class(long_logn[(size_t)k]);
-            const int dep = k >= slots ? k - slots : -1;
-            for (int j = 0; j < c->tiles1; ++j)
-                items.push_back(make_int4(kPass1 + c->logn, k, j, dep));
-        }
-        if (k >= lag && k - lag < nlong) {
-            const int lt = k - lag;
-            const RaggedClass* c = ragged_class(long_logn[(size_t)lt]);
-            for (int j = 0; j < c->tiles2; ++j)
-                items.push_back(make_int4(kPass2 + c->logn, lt, j, lt));
-        }
-    }
-    // row items, longest first
+    // row items, longest first, eight to a cluster item
     std::vector<long long> order_off;
+    std::vector<int4> items;
     for (int l = kMaxLogN; l >= 2; --l) {
         const RaggedClass* c = ragged_class(l);
         if (c->large) continue;
@@ -411,6 +389,9 @@ sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform
         for (int s0 = 0; s0 < n_in; s0 += c->per_item)
             items.push_back(make_int4(l, first + s0, std::min(c->per_item, n_in - s0), 0));
     }
+    for (int i0 = 0; i0 < (int)items.size(); i0 += kRaggedCluster)
+        citems.push_back(make_int4(items[(size_t)i0].x, i0,
+                                   std::min(kRaggedCluster, (int)items.size() - i0), 0));
 
     sdft_plan* p = new (std::nothrow) sdft_plan();
     if (!p) { fail(SDFT_ERR_ALLOC); return nullptr; }
@@ -424,9 +405,8 @@ sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform
     r.on = true;
     r.uniform = uniform;
     r.count = count;
-    r.nitems = (int)items.size();
+    r.nitems = (int)citems.size();
     r.nlong = nlong;
-    r.slots = slots;
     r.classes = classes;
     int status = SDFT_OK;
     cudaStream_t st = nullptr;
@@ -440,8 +420,9 @@ sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform
             status = SDFT_ERR_CUDA; break;
         }
         if (ragged_prepare() != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
-        p->occupancy = ragged_blocks_per_sm();
-        p->grid = std::max(1, p->occupancy) * sms;
+        p->grid = ragged_resident_ctas();
+        if (p->grid < kRaggedCluster) { status = SDFT_ERR_CUDA; break; }
+        p->occupancy = (p->grid + sms - 1) / sms;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             status = SDFT_ERR_CUDA; break;
         }
@@ -452,25 +433,19 @@ sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform
         const size_t nl = (size_t)std::max(nlong, 1);
         if (cudaMalloc(&p->d_tw, tw_total * sizeof(float2)) != cudaSuccess ||
             cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&r.d_sync, (1 + 2 * nl) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&r.d_sync, 2 * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&r.d_offsets, std::max<size_t>(order_off.size(), 1) * sizeof(long long)) != cudaSuccess ||
             cudaMalloc(&r.d_items, std::max<size_t>(items.size(), 1) * sizeof(int4)) != cudaSuccess ||
-            cudaMalloc(&r.d_long_offsets, nl * sizeof(long long)) != cudaSuccess ||
-            cudaMalloc(&r.d_long_slot, nl * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&r.d_tiles2, nl * sizeof(int)) != cudaSuccess) {
+            cudaMalloc(&r.d_citems, std::max<size_t>(citems.size(), 1) * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc(&r.d_long_offsets, nl * sizeof(long long)) != cudaSuccess) {
             status = SDFT_ERR_ALLOC; break;
         }
-        if (slots > 0) {
-            const size_t bytes = (size_t)slots * (size_t)ragged_slot_size() * sizeof(float2);
-            if (cudaMalloc(&p->d_scratch, bytes) != cudaSuccess) { status = SDFT_ERR_ALLOC; break; }
-        }
         if (cudaMemsetAsync(p->d_status, 0, sizeof(int), st) != cudaSuccess ||
-            cudaMemsetAsync(r.d_sync, 0, (1 + 2 * nl) * sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(r.d_sync, 0, 2 * sizeof(int), st) != cudaSuccess ||
             !up(r.d_offsets, order_off.data(), order_off.size() * sizeof(long long)) ||
             !up(r.d_items, items.data(), items.size() * sizeof(int4)) ||
-            !up(r.d_long_offsets, long_off.data(), long_off.size() * sizeof(long long)) ||
-            !up(r.d_long_slot, long_slot.data(), long_slot.size() * sizeof(int)) ||
-            !up(r.d_tiles2, tiles2.data(), tiles2.size() * sizeof(int))) {
+            !up(r.d_citems, citems.data(), citems.size() * sizeof(int4)) ||
+            !up(r.d_long_offsets, long_off.data(), long_off.size() * sizeof(long long))) {
             status = SDFT_ERR_CUDA; break;
         }
         if (make_w64(&p->w64, p->d_tw, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
@@ -774,7 +749,7 @@ int sdft_plan_set_wait_limit(sdft_plan* plan, int polls) {
 int sdft_plan_inject_unreachable_wait(sdft_plan* plan, int on) {
     if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
     if (!plan->rag.on || plan->rag.nlong == 0) return fail(SDFT_ERR_INVALID_ARG);
-    plan->rag.dep_extra = on ? 1 : 0;
+    plan->rag.inject = on ? 1 : 0;
     return SDFT_OK;
 }
 
@@ -816,10 +791,9 @@ int sdft_plan_describe(const sdft_plan* plan, char* buf, int64_t len) {
         const KernelInfo* q = queue_candidate(log2_exact(plan->n));
         return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
                              "%s; one persistent launch (graph: counter memset + kernel), %d "
-                             "threads/CTA, %zu B smem, grid %d (occupancy %d), %d work items, "
-                             "%d scratch slots",
+                             "threads/CTA, %zu B smem, clusters of %d, grid %d, %d cluster items",
                              q ? q->name : "work queue", ragged_threads(), ragged_smem(),
-                             plan->grid, plan->occupancy, plan->rag.nitems, plan->rag.slots);
+                             kRaggedCluster, plan->grid, plan->rag.nitems);
     }
     if (plan->rag.on) {
         char cls[128] = {0};
@@ -830,9 +804,10 @@ int sdft_plan_describe(const sdft_plan* plan, char* buf, int64_t len) {
         return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
                              "ragged: %lld transforms, %lld points, lengths {%s}; one persistent "
                              "launch (graph: counter memset + kernel), %d threads/CTA, %zu B smem, "
-                             "grid %d, %d work items",
+                             "clusters of %d, grid %d, %d cluster items",
                              (long long)plan->rag.count, (long long)plan->points, cls,
-                             ragged_threads(), ragged_smem(), plan->grid, plan->rag.nitems);
+                             ragged_threads(), ragged_smem(), kRaggedCluster, plan->grid,
+                             plan->rag.nitems);
     }
     return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
                          "%s; %d threads/CTA, %zu B smem, grid %d (occupancy %d), "

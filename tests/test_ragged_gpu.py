@@ -83,7 +83,8 @@ def test_every_class_and_many_items():
 
 
 # uniform-plan schedule with the same radix split as the ragged kernel's routine
-SAME_SCHEDULE = {16: 0, 1024: 0, 4096: 0, 32768: 0, 65536: 0}
+# (for N >= 16384 the cluster kernel)
+SAME_SCHEDULE = {16: 0, 1024: 0, 4096: 0, 16384: 3, 32768: 2, 65536: 2}
 
 
 def test_matches_uniform_plans_bitwise():
@@ -92,7 +93,7 @@ def test_matches_uniform_plans_bitwise():
     tables)."""
     from paper_2504_07264_gb300 import Plan
     from paper_2504_07264_gb300 import sdft as S
-    for n, cnt in ((16, 700), (1024, 37), (4096, 9), (32768, 5), (65536, 3)):
+    for n, cnt in ((16, 700), (1024, 37), (4096, 9), (16384, 7), (32768, 5), (65536, 3)):
         lengths = np.full(cnt, n, dtype=np.int64)
         xr, xi, _ = _ragged_inputs(lengths, 44)
         with Plan(lengths=lengths) as rp:
@@ -108,9 +109,9 @@ def test_matches_uniform_plans_bitwise():
 
 
 def test_bounded_wait_times_out_and_recovers():
-    """An unreachable dependency (planted on the host) makes the device-side
-    waits give up: the status word reports SDFT_ERR_TIMEOUT, the kernel
-    returns, and the same plan computes correctly afterwards."""
+    """A wait for a word that nothing sets (planted on the host) gives up: the
+    status word reports SDFT_ERR_TIMEOUT, the kernel returns, and the same
+    plan computes correctly afterwards."""
     import torch
 
     from paper_2504_07264_gb300 import Plan
