@@ -1,5 +1,7 @@
 """Every compiled schedule of every length matches the oracle (GPU), and the
 autotuner picks one of them."""
+import re
+
 import numpy as np
 import pytest
 
@@ -71,7 +73,7 @@ def _cluster_indices(n):
             if "cluster of" in S.sdft_schedule_describe(n, 0, i)]
 
 
-@pytest.mark.parametrize("logn,idx", [(m, i) for m in (14, 15, 16) for i in _cluster_indices(1 << m)])
+@pytest.mark.parametrize("logn,idx", [(m, i) for m in (13, 14, 15, 16) for i in _cluster_indices(1 << m)])
 def test_cluster_kernel_persistent_loop(logn, idx):
     """The cluster kernels with more transforms than resident clusters: every
     cluster runs several transforms, and the last one is ragged against the
@@ -83,8 +85,9 @@ def test_cluster_kernel_persistent_loop(logn, idx):
     prev = S.sdft_schedule_selected(n, 0)
     try:
         assert S.sdft_schedule_select(n, 0, idx) == S.SDFT_OK
+        q = int(re.search(r"cluster of (\d+) CTAs", S.sdft_schedule_describe(n, 0, idx)).group(1))
         with Plan(n, 1) as probe:
-            clusters = probe.grid // (n // 8192)
+            clusters = probe.grid // q
         batch = 2 * clusters + 3
         xr, xi = W.normal_planes(n, batch, seed=950 + logn)
         with Plan(n, batch) as plan:
