@@ -14,6 +14,7 @@
 // conjugates, i.e. the transposed 2x2 blocks omega^(i,q)^T.
 #pragma once
 
+#include "../../include/sdft.h"
 #include "fft_core.cuh"
 #include "launch.h"
 
@@ -170,8 +171,9 @@ cudaError_t rows_launch(const LaunchArgs& a) {
                          a.xi, a.yr, a.yi, a.batch, a.tw, a.w64);
 }
 
+// Name, shape and twiddle tables of a row configuration (no launch hooks).
 template <class CFG>
-KernelInfo rows_info(const char* name) {
+KernelInfo rows_shape(const char* name) {
     using S = typename CFG::S;
     KernelInfo k = {};
     k.name = name;
@@ -192,9 +194,174 @@ KernelInfo rows_info(const char* name) {
     k.tw_entries = CFG::TW_TOTAL;
     k.scratch_per_cta = 0;
     k.launches = 1;
+    return k;
+}
+
+template <class CFG>
+KernelInfo rows_info(const char* name) {
+    KernelInfo k = rows_shape<CFG>(name);
     k.prepare = rows_prepare<CFG>;
     k.blocks_per_sm = rows_blocks_per_sm<CFG>;
     k.launch = rows_launch<CFG>;
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// Prefetching variant: a CTA of 128 threads holds G transforms (4096 points)
+// per tile, and the next tile's rows arrive by 1-D bulk copies (TMA) into a
+// shared input buffer while the current tile runs its register steps, so
+// HBM reads overlap computation inside one CTA as well as across the three
+// CTAs of an SM.  Step 0 gathers from that buffer; the other steps are those
+// of k_rows; the last step stores straight to global memory.
+// ---------------------------------------------------------------------------
+template <class RC, int MINB_ = 3>
+struct RowPfCfg {
+    using RC_ = RC;
+    using S = typename RC::S;
+    static constexpr int G = RC::G;
+    static constexpr int THREADS = RC::THREADS;
+    static constexpr int MINB = MINB_;
+    static constexpr int N = S::N;
+    static constexpr int IN_FLOATS = 2 * G * N;           // [re: G x N][im: G x N]
+    static constexpr size_t SMEM = (size_t)(IN_FLOATS + G * RC::BUF) * sizeof(float);
+    static_assert(S::NS > 1, "transforms with a shared-memory exchange");
+    static_assert((N * 4) % 16 == 0, "bulk copies of whole rows");
+};
+
+template <class CFG, bool ADJ>
+__global__ void __launch_bounds__(CFG::THREADS, CFG::MINB)
+k_rows_pf(const float* xr, const float* xi, float* yr, float* yi, long long batch,
+          const float2* __restrict__ tw, const W64 w, int* status) {
+    using RC = typename CFG::RC_;
+    using S = typename CFG::S;
+    constexpr int N = CFG::N, G = CFG::G;
+    extern __shared__ float4 smem4[];
+    float* const in_re = reinterpret_cast<float*>(smem4);
+    float* const in_im = in_re + G * N;
+    __shared__ __align__(8) uint64_t mbar;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    const int tid = (int)threadIdx.x;
+    const int t = tid & (S::T - 1);
+    const int g = tid >> S::LOGT;
+    float* const s_re = in_re + CFG::IN_FLOATS + g * RC::BUF;
+    float* const s_im = s_re + RC::PLANE;
+    const long long ntiles = (batch + G - 1) / G;
+    // thread 0: the rows of tile `k` into the input buffer
+    auto load = [&](long long k) {
+        const long long first = k * G;
+        const int cnt = (int)((batch - first < G) ? (batch - first) : G);
+        const uint32_t bytes = (uint32_t)cnt * N * 4u;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     :: "r"(mb), "r"(2u * bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"((uint32_t)__cvta_generic_to_shared(in_re)), "l"(xr + first * N), "r"(bytes),
+                        "r"(mb) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"((uint32_t)__cvta_generic_to_shared(in_im)), "l"(xi + first * N), "r"(bytes),
+                        "r"(mb) : "memory");
+    };
+    // bounded wait for the phase of parity `ph`
+    auto wait = [&](uint32_t ph) {
+        for (int i = 0; i < (1 << 21); ++i) {
+            uint32_t ok;
+            asm volatile("{\n\t.reg .pred p;\n\t"
+                         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(ok) : "r"(mb), "r"(ph) : "memory");
+            if (ok) return true;
+        }
+        return false;
+    };
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool pending = false;   // thread 0: a tile load not yet waited for
+    if (tid == 0 && blockIdx.x < ntiles) { load(blockIdx.x); pending = true; }
+    uint32_t ph = 0;
+    auto xw = [&](int L, float r, float i) {
+        const int p = pad32(L);
+        s_re[p] = r;
+        s_im[p] = i;
+    };
+    auto xrd = [&](int L, float& r, float& i) {
+        const int p = pad32(L);
+        r = s_re[p];
+        i = s_im[p];
+    };
+    auto twf = [&](int s, int d, int nl) -> float2 {
+        const int64_t off = (s == 0) ? RC::TW0 : RC::TW1;
+        const int q = (s == 0) ? (S::N >> S::lr(0)) : (S::N >> (S::lr(0) + S::lr(1)));
+        return __ldg(tw + off + (int64_t)d * q + nl);
+    };
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (__syncthreads_or(!wait(ph))) {      // gave up: record it and stop
+            if (tid == 0) atomicCAS(status, 0, SDFT_ERR_TIMEOUT);
+            break;
+        }
+        ph ^= 1;
+        if (tid == 0) pending = false;
+        const long long b = tile * G + g;
+        const bool active = b < batch;
+        float* const gyr = yr + (active ? b : 0) * (long long)N;
+        float* const gyi = yi + (active ? b : 0) * (long long)N;
+        auto ld = [&](int L, float& r, float& i) {
+            r = in_re[g * N + L];
+            i = in_im[g * N + L];
+        };
+        auto st = [&](int k, float r, float i) {
+            if (active) { gyr[k] = r; gyi[k] = i; }
+        };
+        // the first barrier (after the step-0 gather) frees the input buffer
+        // for the next tile and orders this tile's exchange writes after the
+        // previous tile's last exchange reads
+        int nsync = 0;
+        const long long next = tile + gridDim.x;
+        auto sync = [&] {
+            __syncthreads();
+            if (nsync++ == 0 && tid == 0 && next < ntiles) { load(next); pending = true; }
+        };
+        run_steps<S, ADJ, true>(t, w, ld, xw, xrd, twf, st, sync);
+    }
+    if (tid == 0 && pending) wait(ph);   // no tile load left in flight (bounded)
+}
+
+template <class CFG>
+cudaError_t rows_pf_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_rows_pf<CFG, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CFG::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_rows_pf<CFG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)CFG::SMEM);
+}
+
+template <class CFG>
+int rows_pf_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rows_pf<CFG, false>, CFG::THREADS,
+                                                      CFG::SMEM) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <class CFG>
+cudaError_t rows_pf_launch(const LaunchArgs& a) {
+    if (a.adj)
+        return launch_kernel(k_rows_pf<CFG, true>, a.grid, CFG::THREADS, CFG::SMEM, a.stream, a.xr,
+                             a.xi, a.yr, a.yi, a.batch, a.tw, a.w64, a.status);
+    return launch_kernel(k_rows_pf<CFG, false>, a.grid, CFG::THREADS, CFG::SMEM, a.stream, a.xr,
+                         a.xi, a.yr, a.yi, a.batch, a.tw, a.w64, a.status);
+}
+
+template <class CFG>
+KernelInfo rows_pf_info(const char* name) {
+    KernelInfo k = rows_shape<typename CFG::RC_>(name);
+    k.smem = CFG::SMEM;
+    k.prepare = rows_pf_prepare<CFG>;
+    k.blocks_per_sm = rows_pf_blocks_per_sm<CFG>;
+    k.launch = rows_pf_launch<CFG>;
     return k;
 }
 

@@ -1,0 +1,26 @@
+// rows_pf.cu -- row-kernel candidates whose input tiles are prefetched by
+// 1-D bulk copies (k_rows_pf): 128-thread CTAs of 4096 points, three per SM.
+// (For N = 64 .. 256 and 1024 the same form measured slower than the
+// 256-thread kernels, which stay the only candidates there.)
+#include "kernels_rows.cuh"
+
+namespace sdft {
+
+const KernelInfo* rows_pf_candidate(int logn, int idx) {
+    //                                           LOGN LOGE LR0 LR1 LR2  G
+    static const KernelInfo k9 = rows_pf_info<RowPfCfg<RowCfg<9, 5, 5, 4, 0, 8>>>(
+        "N=512: 16 threads/transform, radix [32,16], input tiles prefetched by TMA");
+    static const KernelInfo k11 = rows_pf_info<RowPfCfg<RowCfg<11, 5, 5, 4, 2, 2>>>(
+        "N=2048: 64 threads/transform, radix [32,16,4], input tiles prefetched by TMA");
+    static const KernelInfo k12 = rows_pf_info<RowPfCfg<RowCfg<12, 5, 5, 5, 2, 1>>>(
+        "N=4096: 128 threads/transform, radix [32,32,4], input tiles prefetched by TMA");
+    if (idx != 0) return nullptr;
+    switch (logn) {
+        case 9: return &k9;
+        case 11: return &k11;
+        case 12: return &k12;
+        default: return nullptr;
+    }
+}
+
+}  // namespace sdft

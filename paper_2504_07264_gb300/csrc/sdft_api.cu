@@ -25,6 +25,7 @@ namespace sdft {
 const KernelInfo* rows_candidate_small(int logn, int idx);
 const KernelInfo* rows_candidate_1024(int logn, int idx);
 const KernelInfo* rows_candidate_big(int logn, int idx);
+const KernelInfo* rows_pf_candidate(int logn, int idx);
 
 // The work-queue schedule of a long length (pass-1 / pass-2 items).
 const KernelInfo* queue_candidate(int logn) {
@@ -51,9 +52,17 @@ const KernelInfo* queue_candidate(int logn) {
 
 // Compiled FP32 schedule `idx` for log2 N (null past the last one).
 const KernelInfo* f32_candidate(int logn, int idx) {
-    if (logn >= 1 && logn <= 9) return rows_candidate_small(logn, idx);
+    if (logn >= 1 && logn <= 8) return rows_candidate_small(logn, idx);
     if (logn == 10) return rows_candidate_1024(logn, idx);
-    if (logn >= 11 && logn <= 13) return rows_candidate_big(logn, idx);
+    if (logn == 9 || logn == 11 || logn == 12) {
+        const auto base = logn == 9 ? rows_candidate_small : rows_candidate_big;
+        const KernelInfo* k = base(logn, idx);
+        if (k) return k;
+        int n = 0;
+        while (base(logn, n)) ++n;
+        return idx >= n ? rows_pf_candidate(logn, idx - n) : nullptr;
+    }
+    if (logn == 13) return rows_candidate_big(logn, idx);
     if (logn == 14) {
         const KernelInfo* k = rows_candidate_big(logn, idx);
         if (k) return k;
