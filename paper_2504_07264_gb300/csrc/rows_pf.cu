@@ -1,5 +1,6 @@
 // rows_pf.cu -- row-kernel candidates whose input tiles are prefetched by
-// 1-D bulk copies (k_rows_pf): 128-thread CTAs of 4096 points, three per SM.
+// 1-D bulk copies (k_rows_pf): 128-thread CTAs of 4096 points, three per SM
+// (N = 512 .. 4096), or one 256-thread CTA per SM (N = 8192).
 // (For N = 64 .. 256 and 1024 the same form measured slower than the
 // 256-thread kernels, which stay the only candidates there.)
 #include "kernels_rows.cuh"
@@ -14,11 +15,16 @@ const KernelInfo* rows_pf_candidate(int logn, int idx) {
         "N=2048: 64 threads/transform, radix [32,16,4], input tiles prefetched by TMA");
     static const KernelInfo k12 = rows_pf_info<RowPfCfg<RowCfg<12, 5, 5, 5, 2, 1>>>(
         "N=4096: 128 threads/transform, radix [32,32,4], input tiles prefetched by TMA");
+    // one 8192-point transform per 256-thread CTA: 130 KiB of shared memory,
+    // so one CTA per SM, its next transform always in flight
+    static const KernelInfo k13 = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1>, 1>>(
+        "N=8192: 256 threads/transform, radix [32,32,8], input tiles prefetched by TMA");
     if (idx != 0) return nullptr;
     switch (logn) {
         case 9: return &k9;
         case 11: return &k11;
         case 12: return &k12;
+        case 13: return &k13;
         default: return nullptr;
     }
 }

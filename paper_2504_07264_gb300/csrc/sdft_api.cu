@@ -62,7 +62,13 @@ const KernelInfo* f32_candidate(int logn, int idx) {
         while (base(logn, n)) ++n;
         return idx >= n ? rows_pf_candidate(logn, idx - n) : nullptr;
     }
-    if (logn == 13) return rows_candidate_big(logn, idx);
+    if (logn == 13) {
+        const KernelInfo* k = rows_candidate_big(logn, idx);
+        if (k) return k;
+        int n = 0;
+        while (rows_candidate_big(logn, n)) ++n;
+        return idx >= n ? rows_pf_candidate(logn, idx - n) : nullptr;
+    }
     if (logn == 14) {
         const KernelInfo* k = rows_candidate_big(logn, idx);
         if (k) return k;
