@@ -99,3 +99,38 @@ def test_cluster_kernel_persistent_loop(logn, idx):
             assert plan.sync_status() == S.SDFT_OK
     finally:
         S.sdft_schedule_select(n, 0, prev)
+
+
+def _prefetch_indices(n):
+    from paper_2504_07264_gb300 import build
+    from paper_2504_07264_gb300 import sdft as S
+    build.build()
+    return [i for i in range(S.sdft_schedule_count(n, 0))
+            if "prefetched" in S.sdft_schedule_describe(n, 0, i)]
+
+
+@pytest.mark.parametrize("logn,idx", [(m, i) for m in range(6, 14) for i in _prefetch_indices(1 << m)])
+def test_prefetch_kernel_persistent_loop(logn, idx):
+    """The prefetching row kernels with more tiles than CTAs (every CTA
+    prefetches while it computes) and a last tile with fewer transforms than
+    the CTA holds; both directions against the oracle, the adjoint in place."""
+    from paper_2504_07264_gb300 import Plan
+    from paper_2504_07264_gb300 import sdft as S
+    n = 1 << logn
+    per = int(re.search(r"(\d+) transform\(s\)/CTA tile", S.sdft_schedule_describe(n, 0, idx)).group(1))
+    prev = S.sdft_schedule_selected(n, 0)
+    try:
+        assert S.sdft_schedule_select(n, 0, idx) == S.SDFT_OK
+        with Plan(n, 1) as probe:
+            grid = probe.grid
+        batch = 2 * grid * per + max(1, per // 2) + 1
+        xr, xi = W.normal_planes(n, batch, seed=960 + logn)
+        with Plan(n, batch) as plan:
+            assert "prefetched" in plan.describe()
+            yr, yi = gpu_run(xr, xi, 0, plan=plan)
+            assert rel_l2_rows(yr, yi, *O.dft_factored_dit(xr, xi)).max() <= TOL_F32
+            zr, zi = gpu_run(xr, xi, 1, plan=plan, inplace=True)
+            assert rel_l2_rows(zr, zi, *O.adjoint_factored(xr, xi)).max() <= TOL_F32
+            assert plan.sync_status() == S.SDFT_OK
+    finally:
+        S.sdft_schedule_select(n, 0, prev)
