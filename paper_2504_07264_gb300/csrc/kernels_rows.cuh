@@ -365,4 +365,140 @@ KernelInfo rows_pf_info(const char* name) {
     return k;
 }
 
+// ---------------------------------------------------------------------------
+// Transposing variant for one thread per transform (N = 16, 32).  With each
+// lane loading its own row, a warp's 16-byte loads touch 32 different lines
+// (lanes N * 4 bytes apart), and the L1 serves one line per cycle.  Here each
+// warp moves the rows of its 32 transforms with 16-byte loads whose lanes
+// cover consecutive bytes, passes them to the owning lanes through shared
+// memory padded to an odd row pitch, runs the register DFT, and stores back
+// the same way.  Warps work independently (warp-level barriers only).
+// ---------------------------------------------------------------------------
+template <class RC>
+struct RowTrCfg {
+    using RC_ = RC;
+    using S = typename RC::S;
+    static constexpr int N = S::N;
+    static constexpr int THREADS = RC::THREADS;
+    static constexpr int G = RC::G;
+    static constexpr int PITCH = N + 1;
+    static constexpr int WARP_FLOATS = 2 * 32 * PITCH;
+    static constexpr size_t SMEM = (size_t)(THREADS / 32) * WARP_FLOATS * sizeof(float);
+    static_assert(S::T == 1 && S::NS == 1 && N >= 8 && N <= 32, "one thread per transform");
+    // (at N = 8 the lanes' own 16-byte rows are already two per 32-byte
+    // sector, and this form measured no faster)
+    static_assert(THREADS % 32 == 0, "whole warps");
+};
+
+template <class CFG, bool ADJ>
+__global__ void __launch_bounds__(CFG::THREADS)
+k_rows_tr(const float* xr, const float* xi, float* yr, float* yi, long long batch,
+          const float2* __restrict__ tw, const W64 w) {
+    using S = typename CFG::S;
+    constexpr int N = CFG::N, P = CFG::PITCH, Q4 = N / 4;
+    constexpr int WARPS = CFG::THREADS / 32;
+    extern __shared__ float4 smem4[];
+    const int lane = (int)threadIdx.x & 31;
+    const int warp = (int)threadIdx.x >> 5;
+    float* const t_re = reinterpret_cast<float*>(smem4) + warp * CFG::WARP_FLOATS;
+    float* const t_im = t_re + 32 * P;
+    const long long groups = (batch + 31) / 32;
+    const long long stride = (long long)gridDim.x * WARPS;
+    for (long long grp = (long long)blockIdx.x * WARPS + warp; grp < groups; grp += stride) {
+        const long long first = grp * 32;
+        const int cnt = (int)((batch - first < 32) ? (batch - first) : 32);
+        // 32 rows x N floats per plane: N / 4 warp-wide 16-byte loads,
+        // float4 q of the block = row q / Q4, columns 4 (q % Q4) .. + 3
+        const float4* gr = reinterpret_cast<const float4*>(xr + first * N);
+        const float4* gi = reinterpret_cast<const float4*>(xi + first * N);
+#pragma unroll
+        for (int j = 0; j < Q4; ++j) {
+            const int q = lane + 32 * j;
+            const int row = q / Q4, c = 4 * (q % Q4);
+            if (row < cnt) {
+                const float4 a = gr[q];
+                const float4 b = gi[q];
+                t_re[row * P + c] = a.x; t_re[row * P + c + 1] = a.y;
+                t_re[row * P + c + 2] = a.z; t_re[row * P + c + 3] = a.w;
+                t_im[row * P + c] = b.x; t_im[row * P + c + 1] = b.y;
+                t_im[row * P + c + 2] = b.z; t_im[row * P + c + 3] = b.w;
+            }
+        }
+        __syncwarp();
+        float ar[N], ai[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            ar[i] = t_re[lane * P + i];
+            ai[i] = t_im[lane * P + i];
+        }
+        float orr[N], oi[N];
+        auto ld = [&](int L, float& r, float& i) { r = ar[L]; i = ai[L]; };
+        auto st = [&](int k, float r, float i) { orr[k] = r; oi[k] = i; };
+        auto none_w = [](int, float, float) {};
+        auto none_r = [](int, float&, float&) {};
+        auto twf = [](int, int, int) -> float2 { return make_float2(1.f, 0.f); };
+        run_steps<S, ADJ>(0, w, ld, none_w, none_r, twf, st, [] {});
+        __syncwarp();   // every lane has read its row before the results overwrite it
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            t_re[lane * P + k] = orr[k];
+            t_im[lane * P + k] = oi[k];
+        }
+        __syncwarp();
+        float4* yr4 = reinterpret_cast<float4*>(yr + first * N);
+        float4* yi4 = reinterpret_cast<float4*>(yi + first * N);
+#pragma unroll
+        for (int j = 0; j < Q4; ++j) {
+            const int q = lane + 32 * j;
+            const int row = q / Q4, c = 4 * (q % Q4);
+            if (row < cnt) {
+                yr4[q] = make_float4(t_re[row * P + c], t_re[row * P + c + 1],
+                                     t_re[row * P + c + 2], t_re[row * P + c + 3]);
+                yi4[q] = make_float4(t_im[row * P + c], t_im[row * P + c + 1],
+                                     t_im[row * P + c + 2], t_im[row * P + c + 3]);
+            }
+        }
+        __syncwarp();   // stores have read the tile before the next group fills it
+    }
+    (void)tw;
+}
+
+template <class CFG>
+cudaError_t rows_tr_prepare() {
+    if (CFG::SMEM <= 48 * 1024) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_rows_tr<CFG, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CFG::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_rows_tr<CFG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)CFG::SMEM);
+}
+
+template <class CFG>
+int rows_tr_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rows_tr<CFG, false>, CFG::THREADS,
+                                                      CFG::SMEM) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <class CFG>
+cudaError_t rows_tr_launch(const LaunchArgs& a) {
+    if (a.adj)
+        return launch_kernel(k_rows_tr<CFG, true>, a.grid, CFG::THREADS, CFG::SMEM, a.stream, a.xr,
+                             a.xi, a.yr, a.yi, a.batch, a.tw, a.w64);
+    return launch_kernel(k_rows_tr<CFG, false>, a.grid, CFG::THREADS, CFG::SMEM, a.stream, a.xr,
+                         a.xi, a.yr, a.yi, a.batch, a.tw, a.w64);
+}
+
+template <class CFG>
+KernelInfo rows_tr_info(const char* name) {
+    KernelInfo k = rows_shape<typename CFG::RC_>(name);
+    k.smem = CFG::SMEM;
+    k.prepare = rows_tr_prepare<CFG>;
+    k.blocks_per_sm = rows_tr_blocks_per_sm<CFG>;
+    k.launch = rows_tr_launch<CFG>;
+    return k;
+}
+
 }  // namespace sdft

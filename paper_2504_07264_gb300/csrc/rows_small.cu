@@ -3,8 +3,9 @@
 // transform; N = 64 .. 512 two register steps and one shared-memory exchange
 // (pad words chosen so the warps' two or four transforms fall on disjoint
 // banks).  The other candidates change the radix split, the threads per
-// transform or the register-DFT order (Eq. (6) order, "DIT"); the autotuner
-// times them.
+// transform, the register-DFT order (Eq. (6) order, "DIT") or, for N = 16
+// and 32, move the rows through shared memory by whole lines (k_rows_tr);
+// the autotuner times them.
 #include "kernels_rows.cuh"
 
 namespace sdft {
@@ -23,11 +24,15 @@ const KernelInfo* rows_candidate_small(int logn, int idx) {
     static const KernelInfo k4[] = {
         rows_info<RowCfg<4, 4, 4, 0, 0, 256>>("N=16: 1 thread/transform, radix [16]"),
         rows_info<RowCfg<4, 4, 4, 0, 0, 256, 0, 1, true>>("N=16: 1 thread/transform, radix [16], Eq. (6) order"),
-        rows_info<RowCfg<4, 2, 2, 2, 0, 64, 3>>("N=16: 4 threads/transform, radix [4,4]")};
+        rows_info<RowCfg<4, 2, 2, 2, 0, 64, 3>>("N=16: 4 threads/transform, radix [4,4]"),
+        rows_tr_info<RowTrCfg<RowCfg<4, 4, 4, 0, 0, 256>>>(
+            "N=16: 1 thread/transform, radix [16], rows moved by whole lines through shared memory")};
     static const KernelInfo k5[] = {
         rows_info<RowCfg<5, 5, 5, 0, 0, 128>>("N=32: 1 thread/transform, radix [32]"),
         rows_info<RowCfg<5, 5, 5, 0, 0, 128, 0, 1, true>>("N=32: 1 thread/transform, radix [32], Eq. (6) order"),
-        rows_info<RowCfg<5, 3, 3, 2, 0, 64, 1>>("N=32: 4 threads/transform, radix [8,4]")};
+        rows_info<RowCfg<5, 3, 3, 2, 0, 64, 1>>("N=32: 4 threads/transform, radix [8,4]"),
+        rows_tr_info<RowTrCfg<RowCfg<5, 5, 5, 0, 0, 128>>>(
+            "N=32: 1 thread/transform, radix [32], rows moved by whole lines through shared memory")};
     static const KernelInfo k6[] = {
         rows_info<RowCfg<6, 3, 3, 3, 0, 32, 2>>("N=64: 8 threads/transform, radix [8,8]"),
         rows_info<RowCfg<6, 3, 3, 3, 0, 32, 2, 1, true>>("N=64: 8 threads/transform, radix [8,8], Eq. (6) order")};
