@@ -172,9 +172,16 @@ def cpu_oracle_rate(target_s: float = 10.0, max_batch: int = BATCH) -> dict:
     dt = time.perf_counter() - t0
     what = (f"all {sample} transforms, {passes} passes" if passes > 1
             else f"first {sample} of the {BATCH} transforms")
+    # the same procedure on one core, on a sample sized to ~target_s / 4
+    one = int(max(16, min(max_batch, (target_s / 4) / max(per * used, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.dft_factored_dit(xr64[:one], xi64[:one], threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": passes * sample * N_POINTS / dt / 1e9, "unit": UNIT, "cores": used,
             "kind": "oracle",
-            "sample": f"{what} (N={N_POINTS}, seed 1), Eq. (6) procedure in float64, {dt:.1f} s"}
+            "sample": f"{what} (N={N_POINTS}, seed 1), Eq. (6) procedure in float64, {dt:.1f} s",
+            "one_core": {"value": one * N_POINTS / dt1 / 1e9, "unit": UNIT,
+                         "sample": f"first {one} transforms, {dt1:.1f} s"}}
 
 
 def run_reference(args) -> None:
@@ -293,6 +300,18 @@ def run_ours(args) -> None:
         for _ in range(3):
             copy()
         ms_copy = _time_steps(copy, max(10, args.steps // 4), stream)
+        barrier()
+        # the metric's second arithmetic path: split-BF16 tensor cores, same shape
+        with Plan(N_POINTS, batch, 1) as splan:
+            sf = lambda: splan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
+            sa = lambda: splan.execute(SDFT_ADJOINT, xr, xi, yr, yi, stream)  # noqa: E731
+            for _ in range(3):
+                sf()
+                sa()
+            split_steps = max(10, min(args.steps, 500))
+            ms_sf = _time_steps(sf, split_steps, stream)
+            ms_sa = _time_steps(sa, split_steps, stream)
+            split_desc = splan.describe()
     clocks = clk.summary(m0, m1 if m1 > m0 else None)
     ms_fwd = max_over_ranks(ms_fwd, dist)
     ms_adj = max_over_ranks(ms_adj, dist)
@@ -361,6 +380,13 @@ def run_ours(args) -> None:
                     "frac": achieved_adj / peaks["hbm_gbs"]},
         "copy_ceiling": {"gbs": BYTES_PER_POINT * points / (ms_copy * 1e-3) / 1e9,
                          "what": "torch copy_ of both planes, same shape"},
+        "split_bf16": {
+            "forward": {"value": points / (ms_sf * 1e-3) / 1e9, "unit": UNIT, "ms": ms_sf,
+                        "frac": BYTES_PER_POINT * points / (ms_sf * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+            "adjoint": {"value": points / (ms_sa * 1e-3) / 1e9, "unit": UNIT, "ms": ms_sa,
+                        "frac": BYTES_PER_POINT * points / (ms_sa * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+            "steps": split_steps, "schedule": split_desc,
+            "what": "rank 0's GPU, same inputs, timed after the FP32 region"},
         "e2e": None if e2e_s is None else {
             "value": world * points / e2e_s / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": 2 * points * 4, "d2h_bytes_per_step": 2 * points * 4,
@@ -559,6 +585,42 @@ def run_workload(args) -> None:
         line["sizes"] = rows
         line["metric"] = "planar DFT Gpts/s per N, 2^26 points per step"
         line["value"] = None
+    elif args.workload == "plain":
+        # 1024 transforms of N = 16 (256 KiB moved): a latency-bound call,
+        # reported in microseconds, with its parity against both oracles
+        import numpy as np
+
+        from oracle import oracle
+        from paper_2504_07264_gb300 import SDFT_FORWARD, Plan
+        cfg = workloads.PLAIN
+        n, batch = cfg["n"], cfg["batch"]
+        xr_h, xi_h = workloads.plain()
+        xr = torch.from_numpy(xr_h).cuda()
+        xi = torch.from_numpy(xi_h).cuda()
+        yr = torch.empty_like(xr)
+        yi = torch.empty_like(xi)
+        with Plan(n, batch) as plan:
+            plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)
+            torch.cuda.synchronize()
+            gr = yr.cpu().numpy().astype(np.float64)
+            gi = yi.cpu().numpy().astype(np.float64)
+            errs = {}
+            for name, fn in (("direct", oracle.dft_direct), ("factored", oracle.dft_factored_dit)):
+                rr, ri = fn(xr_h.astype(np.float64), xi_h.astype(np.float64))
+                rows = np.sqrt(((gr - rr) ** 2 + (gi - ri) ** 2).sum(1) / (rr ** 2 + ri ** 2).sum(1))
+                errs[name] = float(rows.max())
+            fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
+            for _ in range(args.warmup):
+                fwd()
+            torch.cuda.synchronize()
+            ms = _time_steps(fwd, args.steps, stream)
+            line.update({"n": n, "batch": batch, "schedule": plan.describe(),
+                         "us_per_call": ms * 1e3, "gpts": n * batch / (ms * 1e-3) / 1e9,
+                         "rel_l2_worst_transform": errs})
+        line["metric"] = "planar DFT, 1024 transforms of N=16 (uniform [-1,1), seed 0): us per call"
+        line["value"] = ms * 1e3
+        line["unit"] = "us"
+        line["higher_is_better"] = False
     print(json.dumps(line), flush=True)
 
 
@@ -573,7 +635,8 @@ def main(argv=None) -> int:
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the host-buffer end-to-end leg (it is on by default)")
     ap.add_argument("--workload",
-                    choices=("bandwidth", "autograd", "precision", "ragged", "sizes", "uniform"),
+                    choices=("bandwidth", "autograd", "precision", "ragged", "sizes", "uniform",
+                             "plain"),
                     default="bandwidth",
                     help="bandwidth (default) is the headline line; the others print one "
                          "single-GPU line of their own")
