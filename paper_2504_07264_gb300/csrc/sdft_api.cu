@@ -27,7 +27,7 @@ const KernelInfo* rows_candidate_1024(int logn, int idx);
 const KernelInfo* rows_candidate_big(int logn, int idx);
 const KernelInfo* rows_pf_candidate(int logn, int idx);
 
-// The work-queue schedule of a long length (pass-1 / pass-2 items).
+// The work-queue schedule of a long length (cluster items of the ragged kernel).
 const KernelInfo* queue_candidate(int logn) {
     static KernelInfo q[17];
     static const bool init = [] {
