@@ -30,12 +30,62 @@ struct RowCfg {
     static constexpr int PLANE = S::N + (S::N >> 5);
     static constexpr int BUF = 2 * PLANE + SBX_;
     static constexpr size_t SMEM = S::NS > 1 ? (size_t)G * BUF * sizeof(float) : 0;
+    // Step-0 rotations W_N^{nl d} (d < R0, nl < Q0 = N / R0).  For Q0 >= 64
+    // (N >= 2048) the full table (N entries, 16 .. 128 KiB) does not stay in
+    // L1 beside 66 KiB of shared memory per CTA, so it is factored,
+    // d = dl + 8 dh: W_N^{nl dl} ([dl][nl], dl < 8) times W_{N/8}^{nl dh}
+    // ([dh][nl], dh < R0 / 8), one extra complex product per rotation.
+    static constexpr int R0 = 1 << S::lr(0), Q0 = S::N / R0;
+    static constexpr bool FACT = S::NS > 1 && R0 >= 16 && Q0 >= 64;
     static constexpr int64_t TW0 = 0;
-    static constexpr int64_t TW1 = S::NS > 1 ? S::tw_entries(0) : 0;
+    static constexpr int64_t TWB = 8 * (int64_t)Q0;          // [dh][nl] when FACT
+    static constexpr int64_t TW1 =
+        S::NS > 1 ? (FACT ? TWB + (R0 / 8) * (int64_t)Q0 : S::tw_entries(0)) : 0;
     static constexpr int64_t TW_TOTAL = TW1 + (S::NS > 2 ? S::tw_entries(1) : 0);
     static_assert(THREADS <= 1024, "CTA too large");
     static_assert(S::T <= 32 || G == 1 || THREADS <= 1024, "");
 };
+
+// The rotation of step s for output digit d of column group nl (see RowCfg).
+template <class CFG>
+__device__ __forceinline__ float2 rows_twiddle(const float2* __restrict__ tw, const int s,
+                                               const int d, const int nl) {
+    using S = typename CFG::S;
+    if constexpr (CFG::FACT) {
+        if (s == 0) {
+            const int dl = d & 7, dh = d >> 3;
+            if (dh == 0) return __ldg(tw + CFG::TW0 + dl * CFG::Q0 + nl);
+            const float2 b = __ldg(tw + CFG::TWB + dh * CFG::Q0 + nl);
+            if (dl == 0) return b;
+            const float2 a = __ldg(tw + CFG::TW0 + dl * CFG::Q0 + nl);
+            return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+        }
+    }
+    const int64_t off = (s == 0) ? CFG::TW0 : CFG::TW1;
+    const int q = (s == 0) ? (S::N >> S::lr(0)) : (S::N >> (S::lr(0) + S::lr(1)));
+    return __ldg(tw + off + (int64_t)d * q + nl);
+}
+
+// The tables rows_twiddle reads, for plan creation; returns their count.
+template <class CFG>
+int rows_tables(TableDesc* t) {
+    using S = typename CFG::S;
+    int n = 0;
+    if (S::NS > 1) {
+        const int64_t nn = S::N;
+        if (CFG::FACT) {
+            t[n++] = TableDesc{nn, 8, CFG::Q0, CFG::TW0};
+            t[n++] = TableDesc{nn / 8, CFG::R0 / 8, CFG::Q0, CFG::TWB};
+        } else {
+            t[n++] = TableDesc{nn, (int64_t)1 << S::lr(0), nn >> S::lr(0), CFG::TW0};
+        }
+        if (S::NS > 2) {
+            const int64_t m1 = nn >> S::lr(0);
+            t[n++] = TableDesc{m1, (int64_t)1 << S::lr(1), m1 >> S::lr(1), CFG::TW1};
+        }
+    }
+    return n;
+}
 
 // One tile of CFG: group g (the caller's `t`, `s_re`, `s_im` belong to it)
 // transforms the row at gxr/gxi into gyr/gyi when `active`.  Every thread of
@@ -60,11 +110,7 @@ __device__ __forceinline__ void rows_tile(const float* gxr, const float* gxi, fl
         r = s_re[p];
         i = s_im[p];
     };
-    auto twf = [&](int s, int d, int nl) -> float2 {
-        const int64_t off = (s == 0) ? CFG::TW0 : CFG::TW1;
-        const int q = (s == 0) ? (S::N >> S::lr(0)) : (S::N >> (S::lr(0) + S::lr(1)));
-        return __ldg(tw + off + (int64_t)d * q + nl);
-    };
+    auto twf = [&](int s, int d, int nl) -> float2 { return rows_twiddle<CFG>(tw, s, d, nl); };
     if constexpr (S::T == 1) {
         // whole row per thread: vector loads into registers, then the step
         // engine reads them by compile-time index.
@@ -181,16 +227,7 @@ KernelInfo rows_shape(const char* name) {
     k.threads = CFG::THREADS;
     k.smem = CFG::SMEM;
     k.transforms_per_cta = CFG::G;
-    k.ntables = 0;
-    if (S::NS > 1) {
-        const int64_t n = S::N;
-        k.tables[k.ntables++] = TableDesc{n, (int64_t)1 << S::lr(0), n >> S::lr(0), CFG::TW0};
-        if (S::NS > 2) {
-            const int64_t m1 = n >> S::lr(0);
-            k.tables[k.ntables++] =
-                TableDesc{m1, (int64_t)1 << S::lr(1), m1 >> S::lr(1), CFG::TW1};
-        }
-    }
+    k.ntables = rows_tables<CFG>(k.tables);
     k.tw_entries = CFG::TW_TOTAL;
     k.scratch_per_cta = 0;
     k.launches = 1;
@@ -291,11 +328,7 @@ k_rows_pf(const float* xr, const float* xi, float* yr, float* yi, long long batc
         r = s_re[p];
         i = s_im[p];
     };
-    auto twf = [&](int s, int d, int nl) -> float2 {
-        const int64_t off = (s == 0) ? RC::TW0 : RC::TW1;
-        const int q = (s == 0) ? (S::N >> S::lr(0)) : (S::N >> (S::lr(0) + S::lr(1)));
-        return __ldg(tw + off + (int64_t)d * q + nl);
-    };
+    auto twf = [&](int s, int d, int nl) -> float2 { return rows_twiddle<RC>(tw, s, d, nl); };
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (__syncthreads_or(!wait(ph))) {      // gave up: record it and stop
             if (tid == 0) atomicCAS(status, 0, SDFT_ERR_TIMEOUT);

@@ -246,20 +246,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_ragged(const RaggedArgs a) {
 
 template <class CFG>
 RaggedClass row_class(int logn) {
-    using S = typename CFG::S;
     RaggedClass c = {};
     c.logn = logn;
     c.per_item = CFG::G;
     c.large = false;
-    c.ntables = 0;
-    if (S::NS > 1) {
-        const int64_t n = S::N;
-        c.tables[c.ntables++] = TableDesc{n, (int64_t)1 << S::lr(0), n >> S::lr(0), CFG::TW0};
-        if (S::NS > 2) {
-            const int64_t m1 = n >> S::lr(0);
-            c.tables[c.ntables++] = TableDesc{m1, (int64_t)1 << S::lr(1), m1 >> S::lr(1), CFG::TW1};
-        }
-    }
+    c.ntables = rows_tables<CFG>(c.tables);
     c.tw_entries = CFG::TW_TOTAL;
     return c;
 }
