@@ -106,14 +106,16 @@ def _prefetch_indices(n):
     from paper_2504_07264_gb300 import sdft as S
     build.build()
     return [i for i in range(S.sdft_schedule_count(n, 0))
-            if "prefetched" in S.sdft_schedule_describe(n, 0, i)]
+            if "prefetched" in S.sdft_schedule_describe(n, 0, i)
+            or "whole lines" in S.sdft_schedule_describe(n, 0, i)]
 
 
-@pytest.mark.parametrize("logn,idx", [(m, i) for m in range(6, 14) for i in _prefetch_indices(1 << m)])
+@pytest.mark.parametrize("logn,idx", [(m, i) for m in range(1, 14) for i in _prefetch_indices(1 << m)])
 def test_prefetch_kernel_persistent_loop(logn, idx):
-    """The prefetching row kernels with more tiles than CTAs (every CTA
-    prefetches while it computes) and a last tile with fewer transforms than
-    the CTA holds; both directions against the oracle, the adjoint in place."""
+    """The prefetching and line-moving row kernels with more tiles than CTAs
+    (every CTA loops, prefetching while it computes) and a last tile with
+    fewer transforms than the CTA holds; both directions against the oracle,
+    the adjoint in place."""
     from paper_2504_07264_gb300 import Plan
     from paper_2504_07264_gb300 import sdft as S
     n = 1 << logn
@@ -126,7 +128,7 @@ def test_prefetch_kernel_persistent_loop(logn, idx):
         batch = 2 * grid * per + max(1, per // 2) + 1
         xr, xi = W.normal_planes(n, batch, seed=960 + logn)
         with Plan(n, batch) as plan:
-            assert "prefetched" in plan.describe()
+            assert S.sdft_schedule_describe(n, 0, idx).split(";")[0] in plan.describe()
             yr, yi = gpu_run(xr, xi, 0, plan=plan)
             assert rel_l2_rows(yr, yi, *O.dft_factored_dit(xr, xi)).max() <= TOL_F32
             zr, zi = gpu_run(xr, xi, 1, plan=plan, inplace=True)
