@@ -371,7 +371,7 @@ cudaError_t split_prepare() {
 // Resident CTAs per SM.  The runtime's occupancy query answers 1 for these
 // TMEM-allocating kernels although registers and shared memory allow more,
 // so the bound is computed from the kernel's own footprint: registers (per
-// warp, in units of 256), shared memory (plus the 1 KiB the driver reserves
+// warp, in units of 256), shared memory (plus the 1 KiB the CUDA runtime reserves
 // per CTA), warps, and the SM's 512 TMEM columns.
 template <class CFG>
 int split_blocks_per_sm() {
