@@ -139,7 +139,7 @@ def test_full_size_bandwidth_config():
     assert rel_l2_rows(gr, gi, rr, ri).max() <= TOL_F32
 
 
-@pytest.mark.parametrize("logn", [5, 10, 15])
+@pytest.mark.parametrize("logn", [5, 10, 12, 15, 16])
 def test_host_buffers_match_device_path(logn):
     import torch
 
