@@ -251,7 +251,7 @@ KernelInfo rows_info(const char* name) {
 // CTAs of an SM.  Step 0 gathers from that buffer; the other steps are those
 // of k_rows; the last step stores straight to global memory.
 // ---------------------------------------------------------------------------
-template <class RC, int MINB_ = 3>
+template <class RC, int MINB_ = 3, int PART_ = 1>
 struct RowPfCfg {
     using RC_ = RC;
     using S = typename RC::S;
@@ -259,7 +259,14 @@ struct RowPfCfg {
     static constexpr int THREADS = RC::THREADS;
     static constexpr int MINB = MINB_;
     static constexpr int N = S::N;
-    static constexpr int IN_FLOATS = 2 * G * N;           // [re: G x N][im: G x N]
+    // PART > 1 (one transform per tile): only the first N / PART points of the
+    // next row are prefetched, the rest are loaded when the tile starts, so
+    // that the input buffer leaves room for a second CTA (N = 8192) or fits
+    // beside the exchange buffer at all (N = 16384).
+    static constexpr int PART = PART_;
+    static constexpr int PN = N / PART;
+    static_assert(PART == 1 || G == 1, "partial prefetch for one transform per tile");
+    static constexpr int IN_FLOATS = 2 * G * PN;          // [re: G x PN][im: G x PN]
     static constexpr size_t SMEM = (size_t)(IN_FLOATS + G * RC::BUF) * sizeof(float);
     static_assert(S::NS > 1, "transforms with a shared-memory exchange");
     static_assert((N * 4) % 16 == 0, "bulk copies of whole rows");
@@ -274,7 +281,7 @@ k_rows_pf(const float* xr, const float* xi, float* yr, float* yi, long long batc
     constexpr int N = CFG::N, G = CFG::G;
     extern __shared__ float4 smem4[];
     float* const in_re = reinterpret_cast<float*>(smem4);
-    float* const in_im = in_re + G * N;
+    float* const in_im = in_re + G * CFG::PN;
     __shared__ __align__(8) uint64_t mbar;
     const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
     const int tid = (int)threadIdx.x;
@@ -287,7 +294,7 @@ k_rows_pf(const float* xr, const float* xi, float* yr, float* yi, long long batc
     auto load = [&](long long k) {
         const long long first = k * G;
         const int cnt = (int)((batch - first < G) ? (batch - first) : G);
-        const uint32_t bytes = (uint32_t)cnt * N * 4u;
+        const uint32_t bytes = (uint32_t)cnt * CFG::PN * 4u;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                      :: "r"(mb), "r"(2u * bytes) : "memory");
@@ -340,9 +347,16 @@ k_rows_pf(const float* xr, const float* xi, float* yr, float* yi, long long batc
         const bool active = b < batch;
         float* const gyr = yr + (active ? b : 0) * (long long)N;
         float* const gyi = yi + (active ? b : 0) * (long long)N;
+        const float* const gxr = xr + (active ? b : 0) * (long long)N;
+        const float* const gxi = xi + (active ? b : 0) * (long long)N;
         auto ld = [&](int L, float& r, float& i) {
-            r = in_re[g * N + L];
-            i = in_im[g * N + L];
+            if (CFG::PART == 1 || L < CFG::PN) {
+                r = in_re[g * CFG::PN + L];
+                i = in_im[g * CFG::PN + L];
+            } else {
+                r = gxr[L];
+                i = gxi[L];
+            }
         };
         auto st = [&](int k, float r, float i) {
             if (active) { gyr[k] = r; gyi[k] = i; }

@@ -75,7 +75,8 @@ const KernelInfo* f32_candidate(int logn, int idx) {
         int n = 0;
         while (rows_candidate_big(logn, n)) ++n;
         if (idx == n) return queue_candidate(14);
-        return idx > n ? cluster_kernel(14, idx - n - 1) : nullptr;
+        if (idx == n + 1) return cluster_kernel(14, 0);
+        return idx == n + 2 ? rows_pf_candidate(14, 0) : nullptr;
     }
     if (logn >= 15 && logn <= 16) {
         if (idx == 0) return queue_candidate(logn);
