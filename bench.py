@@ -517,6 +517,8 @@ def run_workload(args) -> None:
         yr = torch.empty_like(xr)
         yi = torch.empty_like(xi)
         with Plan(lengths=lengths) as plan:
+            # each length's routine form, chosen on this batch by the plan's tuner
+            line["ragged_variants"] = plan.ragged_autotune(xr, xi, yr, yi, reps=5, stream=stream)
             fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
             adj = lambda: plan.execute(SDFT_ADJOINT, xr, xi, yr, yi, stream)  # noqa: E731
             for _ in range(args.warmup):

@@ -167,6 +167,23 @@ SDFT_API int sdft_plan_set_wait_limit(sdft_plan* plan, int polls);
  * fault on the GPU.  SDFT_ERR_INVALID_ARG for plans without long transforms. */
 SDFT_API int sdft_plan_inject_unreachable_wait(sdft_plan* plan, int on);
 
+/* Ragged plans: the row-tile routine of each length N = 32 .. 8192 comes in
+ * two compiled forms, the register DFTs in decimation-in-frequency order
+ * (default) or in the order of Eq. (6).  Bit l of `mask` selects the second
+ * form for N = 2^l (bits 5 .. 13 only; SDFT_ERR_INVALID_ARG otherwise, or for
+ * uniform plans).  The results agree within rounding. */
+SDFT_API int sdft_plan_set_ragged_variants(sdft_plan* plan, unsigned mask);
+/* The current mask (>= 0), or -status. */
+SDFT_API int sdft_plan_ragged_variants(const sdft_plan* plan);
+/* Time the plan's forward call on the caller's device buffers (the plan's
+ * layout, read xr/xi, written yr/yi) with each length's form, one length at a
+ * time, longest first, keeping the Eq. (6) form only where it is faster by
+ * more than 1 %; `reps` timed calls per trial after one untimed call, with
+ * CUDA events on `stream` (synchronises it).  Leaves the chosen mask set and
+ * returns it (>= 0), or -status. */
+SDFT_API int sdft_plan_ragged_autotune(sdft_plan* plan, const float* xr, const float* xi,
+                                       float* yr, float* yi, int reps, void* stream);
+
 /* Wait for `stream`, then read and clear the plan's device status word:
  * SDFT_OK, or SDFT_ERR_TIMEOUT if a bounded device-side wait gave up. */
 SDFT_API int sdft_plan_sync_status(const sdft_plan* plan, void* stream);

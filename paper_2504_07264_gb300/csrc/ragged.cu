@@ -43,6 +43,18 @@ using R10 = RowCfg<10, 5, 5, 5, 0, 8>;
 using R11 = RowCfg<11, 5, 5, 4, 2, 4>;
 using R12 = RowCfg<12, 5, 5, 5, 2, 2>;
 using R13 = RowCfg<13, 5, 5, 5, 3, 1>;
+// the same radix splits with the register DFTs in the order of Eq. (6); a
+// plan picks one of the two per length (RaggedArgs::alt, set by
+// sdft_plan_ragged_autotune)
+using R5D = RowCfg<5, 5, 5, 0, 0, 256, 0, 1, true>;
+using R6D = RowCfg<6, 3, 3, 3, 0, 32, 2, 1, true>;
+using R7D = RowCfg<7, 4, 4, 3, 0, 32, 0, 1, true>;
+using R8D = RowCfg<8, 4, 4, 4, 0, 16, 0, 1, true>;
+using R9D = RowCfg<9, 5, 5, 4, 0, 16, 16, 1, true>;
+using R10D = RowCfg<10, 5, 5, 5, 0, 8, 0, 1, true>;
+using R11D = RowCfg<11, 5, 5, 4, 2, 4, 0, 1, true>;
+using R12D = RowCfg<12, 5, 5, 5, 2, 2, 0, 1, true>;
+using R13D = RowCfg<13, 5, 5, 5, 3, 1, 0, 1, true>;
 
 constexpr size_t smax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kSmem =
@@ -223,19 +235,47 @@ __global__ void __launch_bounds__(kThreads, 2) k_ragged(const RaggedArgs a) {
         }
         int claim = 0;
         if (leader) claim = atomicAdd(a.counter, 1);
+        const bool alt = (a.alt >> rec.x) & 1u;
         switch (rec.x) {
             case 2: ragged_rows<R2, ADJ>(a, rec, smem); break;
             case 3: ragged_rows<R3, ADJ>(a, rec, smem); break;
             case 4: ragged_rows<R4, ADJ>(a, rec, smem); break;
-            case 5: ragged_rows<R5, ADJ>(a, rec, smem); break;
-            case 6: ragged_rows<R6, ADJ>(a, rec, smem); break;
-            case 7: ragged_rows<R7, ADJ>(a, rec, smem); break;
-            case 8: ragged_rows<R8, ADJ>(a, rec, smem); break;
-            case 9: ragged_rows<R9, ADJ>(a, rec, smem); break;
-            case 10: ragged_rows<R10, ADJ>(a, rec, smem); break;
-            case 11: ragged_rows<R11, ADJ>(a, rec, smem); break;
-            case 12: ragged_rows<R12, ADJ>(a, rec, smem); break;
-            case 13: ragged_rows<R13, ADJ>(a, rec, smem); break;
+            case 5:
+                if (alt) ragged_rows<R5D, ADJ>(a, rec, smem);
+                else ragged_rows<R5, ADJ>(a, rec, smem);
+                break;
+            case 6:
+                if (alt) ragged_rows<R6D, ADJ>(a, rec, smem);
+                else ragged_rows<R6, ADJ>(a, rec, smem);
+                break;
+            case 7:
+                if (alt) ragged_rows<R7D, ADJ>(a, rec, smem);
+                else ragged_rows<R7, ADJ>(a, rec, smem);
+                break;
+            case 8:
+                if (alt) ragged_rows<R8D, ADJ>(a, rec, smem);
+                else ragged_rows<R8, ADJ>(a, rec, smem);
+                break;
+            case 9:
+                if (alt) ragged_rows<R9D, ADJ>(a, rec, smem);
+                else ragged_rows<R9, ADJ>(a, rec, smem);
+                break;
+            case 10:
+                if (alt) ragged_rows<R10D, ADJ>(a, rec, smem);
+                else ragged_rows<R10, ADJ>(a, rec, smem);
+                break;
+            case 11:
+                if (alt) ragged_rows<R11D, ADJ>(a, rec, smem);
+                else ragged_rows<R11, ADJ>(a, rec, smem);
+                break;
+            case 12:
+                if (alt) ragged_rows<R12D, ADJ>(a, rec, smem);
+                else ragged_rows<R12, ADJ>(a, rec, smem);
+                break;
+            case 13:
+                if (alt) ragged_rows<R13D, ADJ>(a, rec, smem);
+                else ragged_rows<R13, ADJ>(a, rec, smem);
+                break;
             default: break;   // kIdle
         }
         if (leader) publish_work(a, load_citem(a, claim), next);
@@ -273,6 +313,9 @@ RaggedClass long_class(int logn) {
 }
 
 }  // namespace
+
+// log2 N of the classes with an alternative routine
+unsigned ragged_alt_classes() { return 0x3FE0u; }   // 5 .. 13
 
 const RaggedClass* ragged_class(int logn) {
     static const RaggedClass c[17] = {

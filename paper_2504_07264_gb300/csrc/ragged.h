@@ -33,6 +33,7 @@ struct RaggedArgs {
     int* status;                    // plan status word (SDFT_ERR_TIMEOUT on a wait that gave up)
     int wait_polls;                 // bound of every wait (polls of ~128 ns)
     int inject;                     // tests: every long item first waits for `never` to become 1
+    unsigned alt;                   // bit l: class log2 N = l uses its alternative routine
     const float2* tw[17];           // twiddle tables of each length class (by log2 N)
     W64 w;
 };
@@ -53,5 +54,6 @@ size_t ragged_smem();
 const void* ragged_kernel_fn(bool adj);
 cudaError_t ragged_prepare();
 int ragged_resident_ctas();                  // whole clusters resident over the GPU
+unsigned ragged_alt_classes();               // bit l: class l has an alternative routine
 
 }  // namespace sdft

@@ -127,6 +127,7 @@ struct RaggedState {
     long long* d_long_offsets = nullptr;
     int wait_polls = 1 << 23;          // ~1 s of 128 ns polls
     int inject = 0;                    // tests: long items wait for a word nothing sets
+    unsigned alt = 0;                  // bit l: class l runs its alternative routine
     const float2* tw[17] = {};
     unsigned classes = 0;              // bit l set: some transform has log2 N = l
     cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -294,6 +295,7 @@ int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi,
     a.status = p->d_status;
     a.wait_polls = r.wait_polls;
     a.inject = r.inject;
+    a.alt = r.alt;
     for (int l = 0; l < 17; ++l) a.tw[l] = r.tw[l];
     a.w = p->w64;
     void* kargs[] = {&a};
@@ -866,6 +868,65 @@ int sdft_schedule_selected(int64_t n, int dtype) {
     if (logn < 1 || logn > kMaxLogN) return -fail(SDFT_ERR_UNSUPPORTED_N);
     if (candidate_count(logn, dtype) == 0) return -fail(SDFT_ERR_UNSUPPORTED_DTYPE);
     return dtype == SDFT_F32 ? g_choice[logn].load() : 0;
+}
+
+int sdft_plan_set_ragged_variants(sdft_plan* plan, unsigned mask) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    if (!plan->rag.on || (mask & ~ragged_alt_classes()) != 0) return fail(SDFT_ERR_INVALID_ARG);
+    plan->rag.alt = mask;
+    return SDFT_OK;
+}
+
+int sdft_plan_ragged_variants(const sdft_plan* plan) {
+    if (!plan_alive(plan) || !plan->rag.on) return -fail(SDFT_ERR_INVALID_ARG);
+    return (int)plan->rag.alt;
+}
+
+int sdft_plan_ragged_autotune(sdft_plan* plan, const float* xr, const float* xi, float* yr,
+                              float* yi, int reps, void* stream) {
+    if (!plan_alive(plan)) return -fail(SDFT_ERR_BAD_PLAN);
+    if (!plan->rag.on || reps < 1) return -fail(SDFT_ERR_INVALID_ARG);
+    int s = check_device(plan);
+    if (s == SDFT_OK) s = check_buffers(plan, xr, xi, yr, yi);
+    if (s != SDFT_OK) return -fail(s);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return -fail(SDFT_ERR_CUDA);
+    }
+    RaggedState& r = plan->rag;
+    // milliseconds per forward call with variant mask `m` (one untimed call first)
+    auto time_mask = [&](unsigned m, float& ms) {
+        r.alt = m;
+        int q = run(plan, SDFT_FORWARD, xr, xi, yr, yi, st, plan->batch, nullptr);
+        if (q == SDFT_OK && cudaEventRecord(e0, st) != cudaSuccess) q = SDFT_ERR_CUDA;
+        for (int i = 0; i < reps && q == SDFT_OK; ++i)
+            q = run(plan, SDFT_FORWARD, xr, xi, yr, yi, st, plan->batch, nullptr);
+        if (q == SDFT_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            q = SDFT_ERR_CUDA;
+        ms /= (float)reps;
+        return q;
+    };
+    // greedy, one length class at a time, longest first: keep the
+    // alternative routine only if it is faster by more than 1 %
+    unsigned mask = 0;
+    float best = 0.f;
+    s = time_mask(mask, best);
+    const unsigned cand = ragged_alt_classes() & r.classes;
+    for (int l = kMaxLogN; l >= 0 && s == SDFT_OK; --l) {
+        if (!(cand & (1u << l))) continue;
+        float ms = 0.f;
+        s = time_mask(mask | (1u << l), ms);
+        if (s == SDFT_OK && ms < best * 0.99f) { mask |= 1u << l; best = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    r.alt = mask;
+    if (s != SDFT_OK) return -fail(s);
+    return (int)mask;
 }
 
 int sdft_autotune(int64_t n, int64_t batch, int dtype, const float* xr, const float* xi, float* yr,

@@ -55,6 +55,9 @@ _SIGS = {
     "sdft_plan_set_host_mode": ([_P, ctypes.c_int], ctypes.c_int),
     "sdft_plan_set_grid": ([_P, ctypes.c_int], ctypes.c_int),
     "sdft_plan_set_wait_limit": ([_P, ctypes.c_int], ctypes.c_int),
+    "sdft_plan_set_ragged_variants": ([_P, ctypes.c_uint], ctypes.c_int),
+    "sdft_plan_ragged_variants": ([_P], ctypes.c_int),
+    "sdft_plan_ragged_autotune": ([_P, _P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "sdft_plan_inject_unreachable_wait": ([_P, ctypes.c_int], ctypes.c_int),
     "sdft_plan_grid": ([_P], ctypes.c_int),
     "sdft_execute_noalloc": ([_I64, _I64, ctypes.c_int, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -187,6 +190,18 @@ def sdft_plan_grid(plan) -> int:
 
 def sdft_plan_set_wait_limit(plan, polls: int) -> int:
     return lib().sdft_plan_set_wait_limit(plan, polls)
+
+
+def sdft_plan_set_ragged_variants(plan, mask: int) -> int:
+    return lib().sdft_plan_set_ragged_variants(plan, mask)
+
+
+def sdft_plan_ragged_variants(plan) -> int:
+    return lib().sdft_plan_ragged_variants(plan)
+
+
+def sdft_plan_ragged_autotune(plan, xr, xi, yr, yi, reps: int, stream) -> int:
+    return lib().sdft_plan_ragged_autotune(plan, xr, xi, yr, yi, reps, stream)
 
 
 def sdft_plan_inject_unreachable_wait(plan, on: int) -> int:
@@ -366,6 +381,26 @@ class Plan:
 
     def set_host_mode(self, mode: int) -> None:
         _check(sdft_plan_set_host_mode(self.handle, mode), "sdft_plan_set_host_mode")
+
+    @property
+    def ragged_variants(self) -> int:
+        """Ragged plans: bit l set = length 2^l runs its Eq. (6)-order routine."""
+        v = sdft_plan_ragged_variants(self.handle)
+        if v < 0:
+            raise SdftError(-v, "sdft_plan_ragged_variants")
+        return v
+
+    def set_ragged_variants(self, mask: int) -> None:
+        _check(sdft_plan_set_ragged_variants(self.handle, mask), "sdft_plan_set_ragged_variants")
+
+    def ragged_autotune(self, xr, xi, yr, yi, reps: int = 10, stream=None) -> int:
+        """Time each length's routine forms on these device tensors (the
+        plan's layout) and keep the faster; returns the chosen mask."""
+        v = sdft_plan_ragged_autotune(self.handle, xr.data_ptr(), xi.data_ptr(), yr.data_ptr(),
+                                      yi.data_ptr(), reps, _stream_handle(stream))
+        if v < 0:
+            raise SdftError(-v, "sdft_plan_ragged_autotune")
+        return v
 
     def sync_status(self, stream=None) -> int:
         return sdft_plan_sync_status(self.handle, _stream_handle(stream))

@@ -79,6 +79,9 @@ def test_bad_plan_handles(handle):
     assert S.sdft_execute(handle, 0, 16, 16, 16, 16, 0) == S.SDFT_ERR_BAD_PLAN
     assert S.sdft_execute_host(handle, 0, 16, 16, 16, 16, 0) == S.SDFT_ERR_BAD_PLAN
     assert S.sdft_plan_sync_status(handle, 0) == S.SDFT_ERR_BAD_PLAN
+    assert S.sdft_plan_set_ragged_variants(handle, 0) == S.SDFT_ERR_BAD_PLAN
+    assert S.sdft_plan_ragged_variants(handle) < 0
+    assert S.sdft_plan_ragged_autotune(handle, 16, 16, 16, 16, 1, 0) == -S.SDFT_ERR_BAD_PLAN
     assert S.sdft_last_error() == S.SDFT_ERR_BAD_PLAN
     assert S.sdft_plan_n(handle) == 0 and S.sdft_plan_launches(handle, 0) == 0
     S.sdft_plan_destroy(handle)  # foreign handles are ignored, not freed

@@ -204,3 +204,32 @@ def test_full_ragged_workload_sampled():
         cand = np.nonzero(lengths == (1 << logn))[0]
         pick += list(rng.choice(cand, min(2, cand.size), replace=False))
     assert _check_segments(lengths, off, xr, xi, *hy, 0, sorted(pick)) <= TOL_F32
+
+
+def test_ragged_variants_and_autotune():
+    """Both routine forms of every row class match the oracle, the variant
+    mask is validated, and the plan's tuner leaves a valid mask in place."""
+    import torch
+
+    from paper_2504_07264_gb300 import Plan
+    from paper_2504_07264_gb300 import sdft as S
+    lengths = np.array([1 << l for l in range(2, 17) for _ in range(3)], dtype=np.int64)
+    lengths = np.random.default_rng(48).permutation(lengths)
+    xr, xi, off = _ragged_inputs(lengths, 48)
+    with Plan(lengths=lengths) as plan:
+        assert plan.ragged_variants == 0
+        plan.set_ragged_variants(0x3FE0)
+        assert plan.ragged_variants == 0x3FE0
+        for direction in (0, 1):
+            yr, yi = _run(plan, xr, xi, direction)
+            assert _check_segments(lengths, off, xr, xi, yr, yi, direction) <= TOL_F32
+        with pytest.raises(S.SdftError):
+            plan.set_ragged_variants(1 << 14)
+        dxr, dxi = torch.from_numpy(xr).cuda(), torch.from_numpy(xi).cuda()
+        m = plan.ragged_autotune(dxr, dxi, torch.empty_like(dxr), torch.empty_like(dxi), reps=2)
+        assert m >= 0 and (m & ~0x3FE0) == 0 and plan.ragged_variants == m
+        yr, yi = _run(plan, xr, xi, 0)
+        assert _check_segments(lengths, off, xr, xi, yr, yi, 0) <= TOL_F32
+    with Plan(1024, 4) as uplan:
+        with pytest.raises(S.SdftError):
+            uplan.set_ragged_variants(0)
