@@ -4,7 +4,8 @@ FP32 forward and adjoint at every N = 2 .. 65536 on seeded inputs spanning
 several CTA tiles plus a ragged tail; the full-size N = 1024 x 65536 batch in
 the benchmark's launch configuration on sampled transforms plus Parseval on
 every transform; bit-exact integer bins; in-place calls; host-buffer calls;
-argument errors that need a device.
+the DFT's closed forms and identities (delta, constant, tone, Parseval,
+linearity, F(F(x))); argument errors that need a device.
 """
 import numpy as np
 import pytest
@@ -184,3 +185,47 @@ def test_argument_errors_on_device():
         assert S.sdft_forward(h, p, q, p, q, st) == S.SDFT_OK                    # in place
         torch.cuda.synchronize()
         assert plan.sync_status() == S.SDFT_OK
+
+
+@pytest.mark.parametrize("logn", [1, 2, 5, 8, 10, 11, 13, 14, 15, 16])
+def test_invariants_on_gpu(logn):
+    """The closed forms and identities of the DFT, on the GPU path with its
+    tuned schedule: delta -> ones, constant -> N delta, a tone -> N delta at
+    its bin, Parseval, linearity, and F(F(x))[n] = N x[-n mod N]."""
+    n = 1 << logn
+    k0 = (3 * n) // 4 + (1 if n > 4 else 0)
+    rows = []
+    delta = np.zeros(n, np.float32)
+    delta[0] = 1.0
+    rows.append((delta, np.zeros(n, np.float32)))
+    rows.append((np.full(n, 0.5, np.float32), np.full(n, -0.25, np.float32)))
+    ang = 2.0 * np.pi * ((k0 * np.arange(n)) % n) / n
+    rows.append((np.cos(ang).astype(np.float32), np.sin(ang).astype(np.float32)))
+    xr = np.stack([r for r, _ in rows])
+    xi = np.stack([i for _, i in rows])
+    yr, yi = (v.astype(np.float64) for v in gpu_run(xr, xi, 0))
+    tol = 4e-6 * n
+    assert np.abs(yr[0] - 1.0).max() < tol and np.abs(yi[0]).max() < tol
+    expect_r = np.zeros(n)
+    expect_i = np.zeros(n)
+    expect_r[0], expect_i[0] = 0.5 * n, -0.25 * n
+    assert np.abs(yr[1] - expect_r).max() < tol and np.abs(yi[1] - expect_i).max() < tol
+    expect_r = np.zeros(n)
+    expect_r[k0 % n] = n
+    assert np.abs(yr[2] - expect_r).max() < tol and np.abs(yi[2]).max() < tol
+    # Parseval, linearity and F(F(x)) on random rows
+    a_r, a_i = W.normal_planes(n, 4, seed=700 + logn)
+    b_r, b_i = W.normal_planes(n, 4, seed=800 + logn)
+    fa = [v.astype(np.float64) for v in gpu_run(a_r, a_i, 0)]
+    fb = [v.astype(np.float64) for v in gpu_run(b_r, b_i, 0)]
+    e_in = (a_r.astype(np.float64) ** 2 + a_i.astype(np.float64) ** 2).sum(1) * n
+    e_out = (fa[0] ** 2 + fa[1] ** 2).sum(1)
+    assert np.abs(e_out - e_in).max() <= 1e-5 * e_in.max()
+    c_r = (2.0 * a_r - 3.0 * b_r).astype(np.float32)
+    c_i = (2.0 * a_i - 3.0 * b_i).astype(np.float32)
+    fc = [v.astype(np.float64) for v in gpu_run(c_r, c_i, 0)]
+    assert rel_l2_rows(fc[0], fc[1], 2.0 * fa[0] - 3.0 * fb[0], 2.0 * fa[1] - 3.0 * fb[1]).max() < 4e-6
+    ffr, ffi = (v.astype(np.float64) for v in gpu_run(*gpu_run(a_r, a_i, 0), 0))
+    rev = (-np.arange(n)) % n
+    assert rel_l2_rows(ffr, ffi, n * a_r[:, rev].astype(np.float64),
+                       n * a_i[:, rev].astype(np.float64)).max() < 4e-6
