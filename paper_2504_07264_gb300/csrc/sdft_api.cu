@@ -17,6 +17,8 @@
 #include <vector>
 
 #include "../../include/sdft.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.h"
 #include "ragged.h"
 #include "split.h"
@@ -97,6 +99,14 @@ constexpr uint64_t kMagic = 0x53444654504c414eull;  // "SDFTPLAN"
 constexpr int kMaxLogN = 16;
 
 thread_local int g_last_error = SDFT_OK;
+
+// NVTX range around an entry point (visible in Nsight tools; a no-op otherwise)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int fail(int status) {
     g_last_error = status;
@@ -519,6 +529,7 @@ const char* sdft_status_string(int status) {
 sdft_plan* plan_create_idx(int64_t n, int64_t batch, int dtype, int idx);
 
 sdft_plan* sdft_plan_create(int64_t n, int64_t batch, int dtype) {
+    NvtxRange range("sdft_plan_create");
     const int logn = log2_exact(n);
     const int idx = (logn >= 1 && logn <= kMaxLogN && dtype == SDFT_F32) ? g_choice[logn].load() : 0;
     return plan_create_idx(n, batch, dtype, idx);
@@ -612,6 +623,7 @@ sdft_plan* plan_create_idx(int64_t n, int64_t batch, int dtype, int idx) {
 }
 
 sdft_plan* sdft_plan_create_ragged(const int64_t* lengths, int64_t count, int dtype) {
+    NvtxRange range("sdft_plan_create_ragged");
     if (lengths == nullptr || count < 1 || count > ((int64_t)1 << 31)) {
         fail(SDFT_ERR_INVALID_ARG);
         return nullptr;
@@ -645,6 +657,7 @@ void sdft_plan_destroy(sdft_plan* plan) {
 
 int sdft_execute(const sdft_plan* plan, int direction, const float* xr, const float* xi,
                  float* yr, float* yi, void* stream) {
+    NvtxRange range(direction == SDFT_ADJOINT ? "sdft_adjoint" : "sdft_forward");
     if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
     if (direction != SDFT_FORWARD && direction != SDFT_ADJOINT) return fail(SDFT_ERR_INVALID_ARG);
     int s = check_buffers(plan, xr, xi, yr, yi);
@@ -669,6 +682,7 @@ int sdft_adjoint(const sdft_plan* plan, const float* xr, const float* xi, float*
 
 int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const float* xi, float* yr,
                       float* yi, void* stream) {
+    NvtxRange range("sdft_execute_host");
     if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
     if (direction != SDFT_FORWARD && direction != SDFT_ADJOINT) return fail(SDFT_ERR_INVALID_ARG);
     if (!xr || !xi || !yr || !yi) return fail(SDFT_ERR_INVALID_ARG);
@@ -884,6 +898,7 @@ int sdft_plan_ragged_variants(const sdft_plan* plan) {
 
 int sdft_plan_ragged_autotune(sdft_plan* plan, const float* xr, const float* xi, float* yr,
                               float* yi, int reps, void* stream) {
+    NvtxRange range("sdft_plan_ragged_autotune");
     if (!plan_alive(plan)) return -fail(SDFT_ERR_BAD_PLAN);
     if (!plan->rag.on || reps < 1) return -fail(SDFT_ERR_INVALID_ARG);
     int s = check_device(plan);
@@ -931,6 +946,7 @@ int sdft_plan_ragged_autotune(sdft_plan* plan, const float* xr, const float* xi,
 
 int sdft_autotune(int64_t n, int64_t batch, int dtype, const float* xr, const float* xi, float* yr,
                   float* yi, int reps, float* ms_out, void* stream) {
+    NvtxRange range("sdft_autotune");
     const int logn = log2_exact(n);
     if (logn < 1 || logn > kMaxLogN) return -fail(SDFT_ERR_UNSUPPORTED_N);
     if (batch < 1 || reps < 1) return -fail(SDFT_ERR_INVALID_ARG);
