@@ -24,10 +24,13 @@
 // mbarrier.  Data moves in bulk (TMA, 1-D): the block matrices once per CTA,
 // each tile's input into a shared buffer -- the next tile's while the current
 // one is in its GEMMs -- and each tile's output from shared memory.  Operands
-// are K-major, no swizzle: 8-row x 16-byte core matrices, K-adjacent core
-// matrices 128 B apart, 8-row groups K/8*128 B apart; every thread writes its
-// row as 16-byte core-matrix rows.  The GEMM-2 operand is the GEMM-1 result
-// transposed per transform, which goes through a padded float32 buffer.
+// have no swizzle: 8 x 16-byte core matrices, K-adjacent core matrices 128 B
+// apart, M-adjacent ones K/8*128 B apart.  The GEMM-1 operand is K-major:
+// thread (b, c) writes its row as 16-byte core-matrix rows.  The GEMM-2
+// operand is the GEMM-1 result transposed per transform; it is stored
+// MN-major, so that thread (b, c), holding column c of transform b's GEMM-2
+// operand after the rotation, writes 8 consecutive rows (b, d) per 16 bytes
+// and no float32 transpose is needed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -54,20 +57,18 @@ struct SplitCfg {
     static constexpr int B_BYTES = NM * K * 2;
     static constexpr int TILE_FLOATS = TPT * N;               // one plane of a tile
     static constexpr int X_BYTES = 2 * TILE_FLOATS * 4;       // input tile, both planes
-    static constexpr int T_BYTES = 2 * ROWS * (R + 1) * 4;    // padded transpose buffer
     // R = 16: the next tile's input is prefetched into its own buffer during
     // the GEMMs.  R = 32: the input tile shares the operand region (loaded at
     // the start of each tile), which keeps 4 CTAs per SM within shared memory.
     static constexpr bool PREFETCH = (R == 16);
-    // the region holding the GEMM operands (A hi, A lo), then the transpose
-    // buffer, then the output tile (and for R = 32 first the input tile)
-    static constexpr int AREG_BYTES =
-        (2 * A_BYTES > T_BYTES ? (2 * A_BYTES > X_BYTES ? 2 * A_BYTES : X_BYTES)
-                               : (T_BYTES > X_BYTES ? T_BYTES : X_BYTES));
+    // the region holding the GEMM operands (A hi, A lo), then the output tile
+    // (and for R = 32 first the input tile)
+    static constexpr int AREG_BYTES = 2 * A_BYTES > X_BYTES ? 2 * A_BYTES : X_BYTES;
     static constexpr int TMEM_COLS = 2 * NM;    // D1 and D2 (64 or 128 columns)
     static constexpr int MAX_CTAS = 512 / TMEM_COLS;
     static constexpr int MINB = MAX_CTAS > 4 ? 4 : MAX_CTAS;
-    static constexpr uint32_t IDESC = tc::idesc_f16(FP16, ROWS, NM);
+    static constexpr uint32_t IDESC = tc::idesc_f16(FP16, ROWS, NM);          // GEMM 1
+    static constexpr uint32_t IDESC2 = tc::idesc_f16(FP16, ROWS, NM, true);   // GEMM 2: A MN-major
     static constexpr int OFF_X = 0, OFF_A = PREFETCH ? X_BYTES : 0, OFF_B = OFF_A + AREG_BYTES;
     // x tile, operand region, B hi, B lo, plus alignment slack; raised so that
     // no more CTAs fit on an SM (228 KiB) than its 512 TMEM columns can serve.
@@ -83,6 +84,12 @@ __host__ __device__ constexpr uint32_t kmaj(int row, int k, int sbo) {
     return (uint32_t)((row & 7) * 16 + (row >> 3) * sbo + (k & 7) * 2 + (k >> 3) * 128);
 }
 
+// byte offset of elements (rows m .. m + 7, column k), m a multiple of 8, in
+// an MN-major, no-swizzle operand with the same core-matrix distances
+__host__ __device__ constexpr uint32_t kmn8(int m, int k, int sbo) {
+    return (uint32_t)((m >> 3) * sbo + (k >> 3) * 128 + (k & 7) * 16);
+}
+
 template <bool FP16>
 __device__ __forceinline__ void split16(const float v, uint16_t& hi, uint16_t& lo) {
     if constexpr (FP16) {
@@ -96,26 +103,41 @@ __device__ __forceinline__ void split16(const float v, uint16_t& hi, uint16_t& l
     }
 }
 
-// Split 8 consecutive K values of a row into hi and lo parts and store them as
-// the row's 16-byte segment of one core matrix in each operand.
+// Split the pair (a, b) into hi and lo parts, two values per conversion; the
+// first value in the low half of each word.  Same rounding as split16.
+template <bool FP16>
+__device__ __forceinline__ void split16x2(const float a, const float b, uint32_t& hi,
+                                          uint32_t& lo) {
+    if constexpr (FP16) {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    }
+}
+
+// Split 8 consecutive values (along K for a K-major operand, along M for an
+// MN-major one) into hi and lo parts and store them as one 16-byte
+// core-matrix row in each operand.
 template <bool FP16>
 __device__ __forceinline__ void store_row8(uint8_t* a_hi, uint8_t* a_lo, uint32_t off,
                                            const float* v, float scale) {
     uint32_t h[4], l[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        uint16_t h0, l0, h1, l1;
-        split16<FP16>(v[2 * j] * scale, h0, l0);
-        split16<FP16>(v[2 * j + 1] * scale, h1, l1);
-        h[j] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-        l[j] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-    }
+    for (int j = 0; j < 4; ++j) split16x2<FP16>(v[2 * j] * scale, v[2 * j + 1] * scale, h[j], l[j]);
     *reinterpret_cast<uint4*>(a_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(a_lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // D (TMEM columns at dt) = A * B over the three split terms, small terms first.
-template <class CFG>
+template <class CFG, uint32_t IDESC>
 __device__ __forceinline__ void issue_gemm(uint32_t dt, uint32_t a_hi, uint32_t a_lo,
                                            uint32_t b_hi, uint32_t b_lo) {
     const uint32_t as[3] = {a_hi, a_lo, a_hi};
@@ -126,7 +148,7 @@ __device__ __forceinline__ void issue_gemm(uint32_t dt, uint32_t a_hi, uint32_t 
         for (int kk = 0; kk < CFG::K / 16; ++kk) {
             const uint64_t ad = tc::smem_desc(as[term] + kk * 256, CFG::LBO, CFG::SBO);
             const uint64_t bd = tc::smem_desc(bs[term] + kk * 256, CFG::LBO, CFG::SBO);
-            tc::mma_f16(dt, ad, bd, CFG::IDESC, (term | kk) != 0);
+            tc::mma_f16(dt, ad, bd, IDESC, (term | kk) != 0);
         }
 }
 
@@ -169,8 +191,6 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
     float* const x_im = x_re + TF;
     uint8_t* const a_hi = sm + CFG::OFF_A;                            // GEMM operands
     uint8_t* const a_lo = a_hi + CFG::A_BYTES;
-    float* const t_re = reinterpret_cast<float*>(sm + CFG::OFF_A);    // transpose (aliases A)
-    float* const t_im = t_re + CFG::ROWS * (R + 1);
     float* const y_re = reinterpret_cast<float*>(sm + CFG::OFF_A);    // output tile (aliases A)
     float* const y_im = y_re + TF;
     uint8_t* const b_hi = sm + CFG::OFF_B;
@@ -252,7 +272,7 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            issue_gemm<CFG>(tbase, sa_hi, sa_lo, sb_hi, sb_lo);
+            issue_gemm<CFG, CFG::IDESC>(tbase, sa_hi, sa_lo, sb_hi, sb_lo);
             tc::mma_commit(mb_mma);
             if (CFG::PREFETCH && tile + gridDim.x < ntiles) {              // prefetch
                 load_tile(tile + gridDim.x);
@@ -262,35 +282,27 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         if (__syncthreads_or(!tc::mbar_wait(mb_mma, ph_mma))) { bad = 1; break; }
         ph_mma ^= 1;
         tc::fence_after_sync();
-        // ---- rotate row (b, c) by W_N^{c d}; transpose each transform (b)
+        // ---- rotate row (b, c) by W_N^{c d}: column c (re) and R + c (im) of
+        // transform b's GEMM-2 operand, rows (b, d), stored MN-major (GEMM 1
+        // has finished reading the operand region)
         float d1[2 * R];
         tmem_row<R>(lane_base, d1);
 #pragma unroll
         for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], __ldg(tw + d * R + c));
-#pragma unroll
-        for (int d = 0; d < R; ++d) {
-            t_re[(bl * R + d) * (R + 1) + c] = d1[d];
-            t_im[(bl * R + d) * (R + 1) + c] = d1[R + d];
-        }
-        __syncthreads();
-        // row (b, d) = tid: the rotated values over c
-#pragma unroll
-        for (int cc = 0; cc < R; ++cc) {
-            d1[cc] = t_re[tid * (R + 1) + cc];
-            d1[R + cc] = t_im[tid * (R + 1) + cc];
-        }
         const int e1 = block_exponent<R>(d1);
         const float s1 = ldexpf(1.f, -e1);
-        __syncthreads();     // transpose reads done before the operand overwrites it
 #pragma unroll
-        for (int k8 = 0; k8 < 2 * R / 8; ++k8)
-            store_row8<CFG::FP16_>(a_hi, a_lo, kmaj(tid, 8 * k8, CFG::SBO), d1 + 8 * k8, s1);
+        for (int j = 0; j < R / 8; ++j) {
+            store_row8<CFG::FP16_>(a_hi, a_lo, kmn8(bl * R + 8 * j, c, CFG::SBO), d1 + 8 * j, s1);
+            store_row8<CFG::FP16_>(a_hi, a_lo, kmn8(bl * R + 8 * j, R + c, CFG::SBO),
+                                   d1 + R + 8 * j, s1);
+        }
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            issue_gemm<CFG>(tbase + NM, sa_hi, sa_lo, sb_hi, sb_lo);
+            issue_gemm<CFG, CFG::IDESC2>(tbase + NM, sa_hi, sa_lo, sb_hi, sb_lo);
             tc::mma_commit(mb_mma);
         }
         if (__syncthreads_or(!tc::mbar_wait(mb_mma, ph_mma))) { bad = 1; break; }

@@ -98,19 +98,23 @@ __device__ __forceinline__ void bulk_wait0() {
 }
 
 // ---- MMA -----------------------------------------------------------------
-// Shared-memory matrix descriptor, no swizzle, K-major: start address, byte
-// distance between core matrices adjacent in K (leading) and in M/N (stride),
-// descriptor version 1.
+// Shared-memory matrix descriptor, no swizzle: start address, byte distance
+// between core matrices adjacent in K (leading) and in M/N (stride),
+// descriptor version 1.  A core matrix is 8 rows of 16 bytes: rows along M/N
+// with 8 K-consecutive elements each (K-major), or rows along K with 8
+// M-consecutive elements each (MN-major, selected in the instruction
+// descriptor).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
 // Instruction descriptor of kind::f16: F32 accumulate, A and B both BF16
-// (fp16 = false) or both F16, both K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_f16(bool fp16, int m, int n) {
+// (fp16 = false) or both F16, B K-major, A K-major or (a_mn) MN-major, shape
+// M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(bool fp16, int m, int n, bool a_mn = false) {
     return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) |
-           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+           ((a_mn ? 1u : 0u) << 15) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 // D[tmem] (+)= A[smem] * B[smem], issued by one thread.
