@@ -21,8 +21,8 @@
 // One CTA of 128 threads (a warpgroup) owns 128 GEMM rows = 128 / R
 // transforms per tile; thread i owns row i and TMEM lane i.  Thread 0 issues
 // the MMAs (6 per GEMM for R = 16, 12 for R = 32) and commits them to an
-// mbarrier.  Data moves in bulk (TMA, 1-D): the block matrices once per CTA,
-// each tile's input into a shared buffer -- the next tile's while the current
+// mbarrier.  Data moves in bulk (TMA, 1-D): the block matrices and the
+// rotation table W_N^{c d} once per CTA, each tile's input into a shared buffer -- the next tile's while the current
 // one is in its GEMMs -- and each tile's output from shared memory.  Operands
 // have no swizzle: 8 x 16-byte core matrices, K-adjacent core matrices 128 B
 // apart, M-adjacent ones K/8*128 B apart.  The GEMM-1 operand is K-major:
@@ -69,14 +69,19 @@ struct SplitCfg {
     static constexpr int MINB = MAX_CTAS > 4 ? 4 : MAX_CTAS;
     static constexpr uint32_t IDESC = tc::idesc_f16(FP16, ROWS, NM);          // GEMM 1
     static constexpr uint32_t IDESC2 = tc::idesc_f16(FP16, ROWS, NM, true);   // GEMM 2: A MN-major
+    // rotation factors W_N^{c d}, d = 1 .. R-1, all c: [d - 1][c]
+    static constexpr int TW_BYTES = (R - 1) * R * 8;
     static constexpr int OFF_X = 0, OFF_A = PREFETCH ? X_BYTES : 0, OFF_B = OFF_A + AREG_BYTES;
-    // x tile, operand region, B hi, B lo, plus alignment slack; raised so that
-    // no more CTAs fit on an SM (228 KiB) than its 512 TMEM columns can serve.
-    static constexpr size_t NEED = (size_t)OFF_B + 2 * (size_t)B_BYTES + 1024;
+    static constexpr int OFF_TW = OFF_B + 2 * B_BYTES;
+    // x tile, operand region, B hi, B lo, rotation table, plus alignment
+    // slack (the base is aligned to 128 bytes); raised so that no more CTAs fit
+    // on an SM (228 KiB) than its 512 TMEM columns can serve.
+    static constexpr size_t NEED = (size_t)OFF_TW + TW_BYTES + 128;
     static constexpr size_t FLOOR = (size_t)(228 * 1024) / (MAX_CTAS + 1) + 1024;
     static constexpr size_t SMEM = NEED > FLOOR ? NEED : FLOOR;
     static_assert(R == 16 || R == 32, "split path covers N = 256 and 1024");
-    static_assert(X_BYTES % 1024 == 0 && AREG_BYTES % 16 == 0, "alignment");
+    static_assert(X_BYTES % 1024 == 0 && AREG_BYTES % 16 == 0 && TW_BYTES % 16 == 0,
+                  "alignment");
 };
 
 // byte offset of element (row, k) in a K-major, no-swizzle operand
@@ -186,7 +191,7 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
     constexpr int TF = CFG::TILE_FLOATS;
     extern __shared__ uint8_t smraw[];
     uint8_t* const sm = reinterpret_cast<uint8_t*>(
-        (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~static_cast<uintptr_t>(1023));
+        (reinterpret_cast<uintptr_t>(smraw) + 127) & ~static_cast<uintptr_t>(127));
     float* const x_re = reinterpret_cast<float*>(sm + CFG::OFF_X);   // input tile
     float* const x_im = x_re + TF;
     uint8_t* const a_hi = sm + CFG::OFF_A;                            // GEMM operands
@@ -194,6 +199,7 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
     float* const y_re = reinterpret_cast<float*>(sm + CFG::OFF_A);    // output tile (aliases A)
     float* const y_im = y_re + TF;
     uint8_t* const b_hi = sm + CFG::OFF_B;
+    const float2* const tw_s = reinterpret_cast<const float2*>(sm + CFG::OFF_TW);
     __shared__ __align__(8) uint64_t mbar[3];
     __shared__ uint32_t tmem_base;
     const int tid = (int)threadIdx.x;
@@ -232,9 +238,11 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
     };
     bool x_pending = false;          // thread 0: an input copy not yet waited for
     if (tid == 0) {
-        // the block matrices (hi then lo) of this direction, once per CTA
-        tc::mbar_expect_tx(mb_b, 2 * CFG::B_BYTES);
+        // the block matrices (hi then lo) of this direction and the rotation
+        // table, once per CTA
+        tc::mbar_expect_tx(mb_b, 2 * CFG::B_BYTES + CFG::TW_BYTES);
         tc::bulk_g2s(sb_hi, bimg + (ADJ ? CFG::B_BYTES : 0), 2 * CFG::B_BYTES, mb_b);
+        tc::bulk_g2s(tc::smem_u32(tw_s), tw + R, CFG::TW_BYTES, mb_b);
         if (CFG::PREFETCH && blockIdx.x < ntiles) { load_tile(blockIdx.x); x_pending = true; }
     }
     int bad = __syncthreads_or(!tc::mbar_wait(mb_b, 0));
@@ -288,7 +296,7 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         float d1[2 * R];
         tmem_row<R>(lane_base, d1);
 #pragma unroll
-        for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], __ldg(tw + d * R + c));
+        for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], tw_s[(d - 1) * R + c]);
         const int e1 = block_exponent<R>(d1);
         const float s1 = ldexpf(1.f, -e1);
 #pragma unroll
@@ -371,13 +379,19 @@ __global__ void k_bimg(uint16_t* dst) {
     img[CFG::B_BYTES / 2 + o] = l;
 }
 
+// Dynamic shared memory, and the largest shared-memory carveout (N = 1024
+// needs all 228 KiB of an SM for 4 CTAs).
 template <class CFG>
 cudaError_t split_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_split<CFG, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CFG::SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_split<CFG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)CFG::SMEM);
+    for (const void* f : {(const void*)k_split<CFG, false>, (const void*)k_split<CFG, true>}) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)CFG::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Resident CTAs per SM.  The runtime's occupancy query answers 1 for these
