@@ -22,9 +22,17 @@ k_cluster(const float* __restrict__ xr, const float* __restrict__ xi, float* __r
     const uint32_t rank = cluster_ctarank();
     const int col = (int)rank * CQ + tid % CQ;
     const int d = (int)rank * AQ + tid % AQ;
+    constexpr uint32_t SHARE = (uint32_t)(CFG::N / CFG::Q) * 4u;   // bytes per plane per CTA
     for (long long t = cluster_id(); t < batch; t += cluster_count()) {
         const float* gxr = xr + t * CFG::N;
         const float* gxi = xi + t * CFG::N;
+        // the cluster's next transform into L2 while this one runs (each CTA
+        // one contiguous share of each plane)
+        const long long tn = t + cluster_count();
+        if (tid == 0 && tn < batch) {
+            prefetch_l2(xr + tn * CFG::N + (long long)rank * (CFG::N / CFG::Q), SHARE);
+            prefetch_l2(xi + tn * CFG::N + (long long)rank * (CFG::N / CFG::Q), SHARE);
+        }
         auto ld = [&](int L, float& r, float& i) {
             r = gxr[col + C * L];
             i = gxi[col + C * L];
