@@ -53,7 +53,7 @@ HEADLINE_SOURCES = ("fft_core.cuh", "kernels_rows.cuh", "rows_1024.cu", "launch.
 # launch of the full 65536 x 1024 workload, from one ncu capture
 # (profiles/fwd_n1024_bandwidth.md), with the source hash it was taken on.
 NCU_TRAFFIC = {
-    "fwd": {"bytes": 536919808 + 485129216, "hash": "fdd59a2352a008fc",
+    "fwd": {"bytes": 536917504 + 485014784, "hash": "b2f369da6465f460",
             "schedule": "N=1024: 32 threads/transform, radix [32,32]"},
 }
 

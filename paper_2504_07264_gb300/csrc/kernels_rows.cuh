@@ -304,6 +304,15 @@ k_rows_pf(const float* xr, const float* xi, float* yr, float* yi, long long batc
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                      :: "r"((uint32_t)__cvta_generic_to_shared(in_im)), "l"(xi + first * N), "r"(bytes),
                         "r"(mb) : "memory");
+        if constexpr (CFG::PART > 1) {
+            // the rest of the row, loaded from global memory when the tile
+            // starts, into L2 meanwhile
+            constexpr uint32_t rest = (uint32_t)(N - CFG::PN) * 4u;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                         :: "l"(xr + first * N + CFG::PN), "r"(rest) : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                         :: "l"(xi + first * N + CFG::PN), "r"(rest) : "memory");
+        }
     };
     // bounded wait for the phase of parity `ph`
     auto wait = [&](uint32_t ph) {

@@ -26,6 +26,16 @@ const KernelInfo* rows_pf_candidate(int logn, int idx) {
     // measured slower)
     static const KernelInfo k14 = rows_pf_info<RowPfCfg<RowCfg<14, 5, 5, 5, 4, 1>, 1, 2>>(
         "N=16384: 512 threads/transform, radix [32,32,16], half of each input row prefetched by TMA");
+    // two 8192-point CTAs per SM, half or a quarter of the next row in
+    // flight in shared memory, the rest of it prefetched into L2
+    static const KernelInfo k13h = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1>, 2, 2>>(
+        "N=8192: 256 threads/transform, radix [32,32,8], half of each input row prefetched by TMA, "
+        "two CTAs/SM");
+    static const KernelInfo k13q = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1>, 2, 4>>(
+        "N=8192: 256 threads/transform, radix [32,32,8], a quarter of each input row prefetched by "
+        "TMA, two CTAs/SM");
+    if (logn == 13 && idx == 1) return &k13h;
+    if (logn == 13 && idx == 2) return &k13q;
     if (idx != 0) return nullptr;
     switch (logn) {
         case 9: return &k9;
