@@ -1,7 +1,9 @@
 // rows_pf.cu -- row-kernel candidates whose input tiles are prefetched by
 // 1-D bulk copies (k_rows_pf): 128-thread CTAs of 4096 points, three per SM
-// (N = 512 .. 4096), one 256-thread CTA per SM (N = 8192), or one 512-thread
-// CTA per SM with half of each row prefetched (N = 16384).
+// (N = 512 .. 4096), one or two 256-thread CTAs per SM (N = 8192; with two, a
+// quarter or half of each next row in shared memory and the rest prefetched
+// into L2), or one 512-thread CTA per SM with half of each row in shared
+// memory and half in L2 (N = 16384).
 // (For N = 64 .. 256 and 1024 the same form measured slower than the
 // 256-thread kernels, which stay the only candidates there.)
 #include "kernels_rows.cuh"
@@ -17,13 +19,12 @@ const KernelInfo* rows_pf_candidate(int logn, int idx) {
     static const KernelInfo k12 = rows_pf_info<RowPfCfg<RowCfg<12, 5, 5, 5, 2, 1>>>(
         "N=4096: 128 threads/transform, radix [32,32,4], input tiles prefetched by TMA");
     // one 8192-point transform per 256-thread CTA: 130 KiB of shared memory,
-    // so one CTA per SM, its next transform always in flight (half of it in
-    // flight with two CTAs per SM measured slower)
+    // so one CTA per SM, its next transform always in flight
     static const KernelInfo k13 = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1>, 1>>(
         "N=8192: 256 threads/transform, radix [32,32,8], input tiles prefetched by TMA");
     // one 16384-point transform per 512-thread CTA, half of the next row in
-    // flight (the whole row does not fit beside the exchange buffer; a quarter
-    // measured slower)
+    // flight in shared memory (the whole row does not fit beside the exchange
+    // buffer) and the other half prefetched into L2
     static const KernelInfo k14 = rows_pf_info<RowPfCfg<RowCfg<14, 5, 5, 5, 4, 1>, 1, 2>>(
         "N=16384: 512 threads/transform, radix [32,32,16], half of each input row prefetched by TMA");
     // two 8192-point CTAs per SM, half or a quarter of the next row in
