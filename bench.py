@@ -240,6 +240,23 @@ def _time_steps(fn, steps: int, stream) -> float:
     return start.elapsed_time(end) / steps
 
 
+def _step_stats(fn, n: int, stream) -> dict:
+    """Median and best of `n` individually timed steps (CUDA events around
+    each call on `stream`), milliseconds."""
+    import statistics
+
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n)]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    evs[-1][1].synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    return {"median_ms": statistics.median(ms), "best_ms": min(ms), "samples": n}
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -295,6 +312,8 @@ def run_ours(args) -> None:
         barrier()
         ms_adj = _time_steps(adj, args.steps, stream)
         barrier()
+        # outside the timed region: 20 individually timed forward steps
+        fwd_stats = _step_stats(fwd, 20, stream)
         # practical ceiling: a same-shape planar copy (both planes)
         copy = lambda: (yr.copy_(xr), yi.copy_(xi))  # noqa: E731
         for _ in range(3):
@@ -378,6 +397,11 @@ def run_ours(args) -> None:
         "adjoint": {"value": world * points / (ms_adj * 1e-3) / 1e9, "unit": UNIT,
                     "ms_per_step": ms_adj, "achieved_gbs": achieved_adj,
                     "frac": achieved_adj / peaks["hbm_gbs"]},
+        "forward_step_stats": {
+            **fwd_stats,
+            "median_value": points / (fwd_stats["median_ms"] * 1e-3) / 1e9,
+            "best_value": points / (fwd_stats["best_ms"] * 1e-3) / 1e9, "unit": UNIT,
+            "what": "rank 0, forward steps timed one by one after the timed region"},
         "copy_ceiling": {"gbs": BYTES_PER_POINT * points / (ms_copy * 1e-3) / 1e9,
                          "what": "torch copy_ of both planes, same shape"},
         "split_bf16": {

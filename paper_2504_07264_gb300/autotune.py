@@ -14,6 +14,7 @@ At import of the package nothing is changed; ``ensure_applied()`` (called by
 else the table shipped with the package (``tuned_schedules.json``), once.
 
 CLI:  python -m paper_2504_07264_gb300.autotune [--out FILE] [--points P] [--reps R]
+                                               [--sizes N [N ...]]
 """
 from __future__ import annotations
 
@@ -143,10 +144,13 @@ def main(argv=None) -> int:
     ap.add_argument("--out", default=os.environ.get("SDFT_TUNE_CACHE") or SHIPPED)
     ap.add_argument("--points", type=int, default=1 << 26)
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--sizes", type=int, nargs="+", default=None,
+                    help="lengths to tune (default: every power of two 2 .. 65536); the "
+                         "others keep their entries in --out")
     a = ap.parse_args(argv)
     from . import build
     build.build()
-    table = tune(points=a.points, reps=a.reps)
+    table = tune(sizes=a.sizes, points=a.points, reps=a.reps)
     save(table, a.out)
     for dtype, per_n in table.items():
         for n, rec in sorted(per_n.items(), key=lambda kv: int(kv[0])):

@@ -1,6 +1,7 @@
 // cluster.cu -- the uniform cluster kernel for N = 16384 .. 65536: one
-// thread-block cluster of N / 8192 CTAs per transform (kernels_cluster.cuh),
-// two CTAs (of different clusters) per SM, a persistent grid: cluster c
+// thread-block cluster of N / 8192 CTAs per transform (kernels_cluster.cuh;
+// N = 32768 also as N / 4096 CTAs of 128 threads), two (four) CTAs of
+// different clusters per SM, a persistent grid: cluster c
 // handles transforms c, c + (clusters), ...  Pass 1 loads straight into
 // registers and pass 2 stores straight from registers.
 #include "kernels_cluster.cuh"
@@ -10,7 +11,7 @@ namespace sdft {
 namespace {
 
 template <class CFG, bool ADJ>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(CFG::THREADS, CFG::MINB)
 k_cluster(const float* __restrict__ xr, const float* __restrict__ xi, float* __restrict__ yr,
           float* __restrict__ yi, const long long batch, const float2* __restrict__ tw,
           const W64 w) {
@@ -52,11 +53,12 @@ k_cluster(const float* __restrict__ xr, const float* __restrict__ xi, float* __r
 
 template <class CFG>
 cudaError_t cluster_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_cluster<CFG, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CFG::SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_cluster<CFG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)CFG::SMEM);
+    for (const void* f : {(const void*)k_cluster<CFG, false>, (const void*)k_cluster<CFG, true>}) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)CFG::SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <class CFG>
@@ -84,7 +86,7 @@ int cluster_resident_ctas() {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
     cudaLaunchAttribute attr[1];
-    const cudaLaunchConfig_t cfg = cluster_config<CFG>(CFG::Q * 2 * sms, nullptr, attr);
+    const cudaLaunchConfig_t cfg = cluster_config<CFG>(CFG::Q * CFG::MINB * sms, nullptr, attr);
     int clusters = 0;
     if (cudaOccupancyMaxActiveClusters(&clusters, k_cluster<CFG, false>, &cfg) != cudaSuccess)
         return 0;
@@ -148,6 +150,10 @@ const KernelInfo* cluster_kernel(int logn, int idx) {
         "N=32768: cluster of 4 CTAs, distributed shared memory, 256 x 128, radix [32,8]x[32,4]");
     static const KernelInfo k16 = cluster_info<Cluster16>(
         "N=65536: cluster of 8 CTAs, distributed shared memory, 256 x 256, radix [32,8]x[32,8]");
+    static const KernelInfo k15q = cluster_info<Cluster15q>(
+        "N=32768: cluster of 8 CTAs of 128 threads, distributed shared memory, 256 x 128, "
+        "radix [32,8]x[32,4]");
+    if (logn == 15 && idx == 1) return &k15q;
     if (idx != 0) return nullptr;
     switch (logn) {
         case 14: return &k14;

@@ -13,7 +13,8 @@
 // [q A/Q, (q+1) A/Q), reading each row's C values from the shared memory of
 // all Q CTAs (ld.shared::cluster).  The intermediate never leaves the chip:
 // HBM sees one read and one write of every point, as for short transforms.
-// Each CTA holds N/Q = 8192 points, 256 threads x 32 values.
+// Each CTA holds N/Q = 8192 points, 256 threads x 32 values (or 4096 points,
+// 128 threads x 32 values).
 //
 // Y is stored column-major, Y[c][d] at c * A + (d ^ (c mod 32)): in pass 1 a
 // warp (32 columns, one d) writes 32 different banks, and in pass 2 a warp
@@ -69,11 +70,12 @@ __device__ __forceinline__ float ld_cluster(uint32_t addr) {
     return v;
 }
 
-template <int LOGA, int LOGC, int LOGQ, class SA, class SC>
+template <int LOGA, int LOGC, int LOGQ, class SA, class SC, int THREADS_ = 256>
 struct ClusterCfg {
     using SA_ = SA;
     using SC_ = SC;
-    static constexpr int THREADS = 256;
+    static constexpr int THREADS = THREADS_;
+    static constexpr int MINB = 512 / THREADS;   // CTAs per SM: 64 K registers / (THREADS x 128)
     static constexpr int Q = 1 << LOGQ;
     static constexpr int A = 1 << LOGA, C = 1 << LOGC, N = A * C, LOGN = LOGA + LOGC;
     static constexpr int LOGCQ = LOGC - LOGQ, CQ = 1 << LOGCQ;   // pass-1 columns per CTA
@@ -81,7 +83,7 @@ struct ClusterCfg {
     static_assert(SA::N == A && SC::N == C, "sub-DFT sizes");
     static_assert(SA::NS == 2 && SC::NS == 2, "two-step sub-DFTs");
     static_assert(CQ * SA::T == THREADS && AQ * SC::T == THREADS, "one CTA per column / row tile");
-    static_assert(CQ >= 32 && AQ >= 32, "a warp covers 32 consecutive columns / rows");
+    static_assert(CQ >= 16 && AQ >= 32, "a warp covers 16 or 32 consecutive columns, 32 rows");
     static_assert(A % 32 == 0, "Y columns are whole 128-byte lines");
     // one buffer for the pass-1 exchange [L][CQ], Y and the pass-2 exchange
     // [L][AQ], each 2 * 8192 floats
@@ -209,5 +211,11 @@ using ClusterR128 = Steps<7, 5, 5, 2, 0>;   // 4 threads x 32 values, radix [32,
 using Cluster14 = ClusterCfg<7, 7, 1, ClusterR128, ClusterR128>;   // 128 x 128, Q = 2
 using Cluster15 = ClusterCfg<8, 7, 2, ClusterR256, ClusterR128>;   // 256 x 128, Q = 4
 using Cluster16 = ClusterCfg<8, 8, 3, ClusterR256, ClusterR256>;   // 256 x 256, Q = 8
+// N = 32768 on clusters of 8 CTAs of 128 threads: 4096 points and 16 columns
+// per CTA, four CTAs (of different transforms) per SM.  (The same form for
+// N = 16384, clusters of 4, and N = 65536, clusters of 16, measured 241 and
+// 158 Gpts/s against 234 and 176 for the 256-thread forms: at N = 65536 only
+// 33 clusters of 16 fit and the pass-2 warps read 64-byte pieces.)
+using Cluster15q = ClusterCfg<8, 7, 3, ClusterR256, ClusterR128, 128>;
 
 }  // namespace sdft
