@@ -177,11 +177,20 @@ def cpu_oracle_rate(target_s: float = 10.0, max_batch: int = BATCH) -> dict:
     t0 = time.perf_counter()
     oracle.dft_factored_dit(xr64[:one], xi64[:one], threads=1)
     dt1 = time.perf_counter() - t0
+    # the binary32 instance of the same procedure, all cores, on the float32
+    # inputs themselves (sample sized like the one-core leg)
+    f32n = int(max(16, min(sample, (target_s / 4) / max(per, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.dft_factored_dit_f32(xr[:f32n], xi[:f32n], threads=used)
+    dt32 = time.perf_counter() - t0
     return {"value": passes * sample * N_POINTS / dt / 1e9, "unit": UNIT, "cores": used,
             "kind": "oracle",
             "sample": f"{what} (N={N_POINTS}, seed 1), Eq. (6) procedure in float64, {dt:.1f} s",
             "one_core": {"value": one * N_POINTS / dt1 / 1e9, "unit": UNIT,
-                         "sample": f"first {one} transforms, {dt1:.1f} s"}}
+                         "sample": f"first {one} transforms, {dt1:.1f} s"},
+            "float32": {"value": f32n * N_POINTS / dt32 / 1e9, "unit": UNIT, "cores": used,
+                        "sample": f"first {f32n} transforms, Eq. (6) procedure in float32, "
+                                  f"{dt32:.1f} s"}}
 
 
 def run_reference(args) -> None:

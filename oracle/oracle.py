@@ -15,6 +15,7 @@ See the C file's header for which equation of the paper each function follows:
   adjoint_direct      transpose of the block matrix Eq. (5)         (O3)
   adjoint_factored    transpose of the Eq. (6) product              (O3f)
   dft_factored_dif    the decimation-in-frequency procedure Eq. (9) (O4)
+  dft_factored_dit_f32  Eq. (6) in binary32 (CPU baseline's FP32 instance) (O2f)
 """
 from __future__ import annotations
 
@@ -32,6 +33,7 @@ _LOCK = threading.Lock()
 _LIBS: dict[int, ctypes.CDLL] = {}
 
 _D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
 _I64P = ctypes.POINTER(ctypes.c_int64)
 
 
@@ -75,6 +77,9 @@ def _load(mutation: int = 0) -> ctypes.CDLL:
         lib.sdft_oracle_direct_bins.restype = ctypes.c_int
         lib.sdft_oracle_dit_stages.argtypes = [ctypes.c_int64, _D, _D]
         lib.sdft_oracle_dit_stages.restype = ctypes.c_int
+        lib.sdft_oracle_factored_dit_f32.argtypes = [ctypes.c_int64, ctypes.c_int64, _F, _F, _F,
+                                                     _F, ctypes.c_int]
+        lib.sdft_oracle_factored_dit_f32.restype = ctypes.c_int
         lib.sdft_oracle_thread_count.argtypes = [ctypes.c_int]
         lib.sdft_oracle_thread_count.restype = ctypes.c_int
         _LIBS[mutation] = lib
@@ -116,6 +121,29 @@ def dft_direct(xr, xi, threads: int = 0, mutation: int = 0):
 def dft_factored_dit(xr, xi, threads: int = 0, mutation: int = 0):
     """O2: the procedure of Eq. (6), N = 2^m."""
     return _batched("sdft_oracle_factored_dit", xr, xi, threads, mutation)
+
+
+def dft_factored_dit_f32(xr, xi, threads: int = 0):
+    """O2f: the procedure of Eq. (6) in binary32 on float32 rows (the CPU
+    baseline's single-precision instance; checked against O2)."""
+    squeeze = np.ndim(xr) == 1
+    xr = np.ascontiguousarray(xr, dtype=np.float32)
+    xi = np.ascontiguousarray(xi, dtype=np.float32)
+    xr = xr.reshape(1, -1) if xr.ndim == 1 else xr
+    xi = xi.reshape(1, -1) if xi.ndim == 1 else xi
+    if xr.shape != xi.shape:
+        raise ValueError("xr and xi must have the same shape")
+    batch, n = xr.shape
+    yr = np.empty_like(xr)
+    yi = np.empty_like(xi)
+    f = _load(0).sdft_oracle_factored_dit_f32
+    rc = f(n, batch, xr.ctypes.data_as(_F), xi.ctypes.data_as(_F), yr.ctypes.data_as(_F),
+           yi.ctypes.data_as(_F), int(threads))
+    if rc != 0:
+        raise ValueError(f"sdft_oracle_factored_dit_f32: rejected n={n} batch={batch} (rc={rc})")
+    if squeeze:
+        return yr[0], yi[0]
+    return yr, yi
 
 
 def dft_factored_dif(xr, xi, threads: int = 0, mutation: int = 0):

@@ -30,6 +30,11 @@
  *                                   S^T D(1)^T W(1)^T ... D(m)^T W(m)^T x.
  *   O4  sdft_oracle_factored_dif    the decimation-in-frequency procedure Eq. (9):
  *                                   y = S D(1) W(1) ... D(m) W(m) x.
+ *   O2f sdft_oracle_factored_dit_f32 Eq. (6) carried out in binary32 (the CPU
+ *                                   baseline's single-precision instance; each
+ *                                   omega^(i,q) entry rounded once from
+ *                                   binary64).  Checked against O2, not a
+ *                                   parity oracle itself.
  *
  * Readings of the paper taken here:
  *   - Eq. (2) prints y = E y; the intended map is y = E x.
@@ -276,6 +281,65 @@ int sdft_oracle_factored_dit(int64_t n, int64_t batch, const double* xr, const d
         }
         free(v);
         free(tmp);
+    }
+    return fail ? -2 : 0;
+}
+
+/* ----------------------------------------------------------------- O2f -- */
+/* Eq. (6) in binary32: S, then D(i) and W(i) for i = 1..m on a float pair
+ * vector, the same index sets as apply_S / apply_D / apply_W.  Each
+ * omega^(i,q) entry is cos/sin of the exact turn q / 2^i in binary64,
+ * rounded once to binary32; every product and sum is a binary32 operation. */
+static void dit_one_f32(int m, const float* xr, const float* xi, float* yr, float* yi,
+                        float* v) {
+    int64_t N = (int64_t)1 << m, len = (int64_t)2 << m;
+    for (int64_t k = 0; k < N; ++k) {                      /* S */
+        int64_t src = bit_reverse(k, m);
+        v[2 * k] = xr[src];
+        v[2 * k + 1] = xi[src];
+    }
+    for (int i = 1; i <= m; ++i) {
+        int64_t block = (int64_t)2 << i, R = (int64_t)1 << (i - 1), half = (int64_t)1 << i;
+        for (int64_t base = 0; base < len; base += block)  /* D(i): lower half of each block */
+            for (int64_t q = 0; q < R; ++q) {
+                double c, s;
+                cos_sin_turn(q, (int64_t)1 << i, &c, &s);
+                float cf = (float)c, sf = (float)s;
+                float* pr = v + base + 2 * R + 2 * q;
+                float a = pr[0], b = pr[1];
+                pr[0] = cf * a + sf * b;
+                pr[1] = -sf * a + cf * b;
+            }
+        for (int64_t base = 0; base < len; base += 2 * half)   /* W(i) */
+            for (int64_t j = 0; j < half; ++j) {
+                float u = v[base + j], w = v[base + j + half];
+                v[base + j] = u + w;
+                v[base + j + half] = u - w;
+            }
+    }
+    for (int64_t k = 0; k < N; ++k) {
+        yr[k] = v[2 * k];
+        yi[k] = v[2 * k + 1];
+    }
+}
+
+int sdft_oracle_factored_dit_f32(int64_t n, int64_t batch, const float* xr, const float* xi,
+                                 float* yr, float* yi, int threads) {
+    int m = ilog2_exact(n);
+    if (m < 0 || batch < 0) return -1;
+    int nt = set_threads(threads);
+    int fail = 0;
+    #pragma omp parallel num_threads(nt) reduction(|: fail)
+    {
+        float* v = (float*)malloc(sizeof(float) * 2 * (size_t)n);
+        if (!v) {
+            fail = 1;
+        } else {
+            #pragma omp for schedule(dynamic, 1)
+            for (int64_t b = 0; b < batch; ++b)
+                dit_one_f32(m, xr + b * n, xi + b * n, yr + b * n, yi + b * n, v);
+        }
+        free(v);
     }
     return fail ? -2 : 0;
 }
