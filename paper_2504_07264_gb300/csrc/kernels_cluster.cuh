@@ -16,8 +16,9 @@
 // Each CTA holds N/Q = 8192 points, 256 threads x 32 values (or 4096 points,
 // 128 threads x 32 values).
 //
-// Y is stored column-major, Y[c][d] at c * A + (d ^ (c mod 32)): in pass 1 a
-// warp (32 columns, one d) writes 32 different banks, and in pass 2 a warp
+// Y is stored column-major, Y[c][d] at c * A + (d ^ (c mod 32)) (2c for
+// 16-column tiles): in pass 1 a warp (32 columns, one d) writes 32 different
+// banks, and in pass 2 a warp
 // (32 consecutive rows d, one column) reads one whole 128-byte line of a
 // remote CTA's shared memory per load.  Remote loads whose lanes touch
 // different lines are split into one network transaction per line.
@@ -87,6 +88,11 @@ struct ClusterCfg {
     static_assert(A % 32 == 0, "Y columns are whole 128-byte lines");
     // one buffer for the pass-1 exchange [L][CQ], Y and the pass-2 exchange
     // [L][AQ], each 2 * 8192 floats
+    // Y swizzle: Y[c][d] at c * A + (d ^ swz(c)), swz(c) = c mod 32, or 2c
+    // with 16-column tiles (a pass-1 warp then writes rows k and k + 1 of 16
+    // columns: 2c keeps the 32 lanes on 32 banks)
+    static constexpr int SWZ_SHIFT = CQ == 16 ? 1 : 0;
+    __host__ __device__ static constexpr int swz(int c) { return (c << SWZ_SHIFT) & 31; }
     static constexpr int WORK_FLOATS = 2 * A * CQ;
     static_assert(2 * C * AQ == WORK_FLOATS, "the passes use equal buffers");
     static constexpr size_t SMEM = (size_t)WORK_FLOATS * sizeof(float);
@@ -115,13 +121,18 @@ __device__ __forceinline__ void pass1(LD ld, MID mid, float* const work, const i
     float* const x_im = work + A * CQ;
     float* const y_re = work;                 // Y[c][dd], swizzled
     float* const y_im = work + A * CQ;
+    // With 16-column tiles a warp holds two rows L of the exchange; rows are
+    // stored with bit 0 flipped when bit 5 is set, so that the step-0 writes
+    // (rows d + 32 ta) and the step-1 reads (rows ta + 8 f + 32 i) of the two
+    // half-warps fall on different banks.
+    auto xrow = [](int L) { return CQ == 16 ? L ^ ((L >> 5) & 1) : L; };
     auto xw = [&](int L, float r, float i) {
-        x_re[L * CQ + sub1] = r;
-        x_im[L * CQ + sub1] = i;
+        x_re[xrow(L) * CQ + sub1] = r;
+        x_im[xrow(L) * CQ + sub1] = i;
     };
     auto xrd = [&](int L, float& r, float& i) {
-        r = x_re[L * CQ + sub1];
-        i = x_im[L * CQ + sub1];
+        r = x_re[xrow(L) * CQ + sub1];
+        i = x_im[xrow(L) * CQ + sub1];
     };
     auto twf = [&](int, int dd, int nl) -> float2 {
         return __ldg(tw + CFG::TWA + dd * (A >> SA::lr(0)) + nl);
@@ -158,8 +169,8 @@ __device__ __forceinline__ void pass1(LD ld, MID mid, float* const work, const i
             }
             float r = re[reg], i = im[reg];
             rot<ADJ>(r, i, wv);
-            y_re[sub1 * A + (k ^ (sub1 & 31))] = r;
-            y_im[sub1 * A + (k ^ (sub1 & 31))] = i;
+            y_re[sub1 * A + (k ^ CFG::swz(sub1))] = r;
+            y_im[sub1 * A + (k ^ CFG::swz(sub1))] = i;
         }
     }
 }
@@ -179,7 +190,7 @@ __device__ __forceinline__ void pass2(ST st, float* const work, const uint32_t y
     // column L of row d lives in CTA L / CQ at Y[L % CQ][d]
     auto ld = [&](int L, float& r, float& i) {
         const int c = L & (CQ - 1);
-        const uint32_t a = map_rank(y_sh + 4u * (uint32_t)(c * A + (d ^ (c & 31))),
+        const uint32_t a = map_rank(y_sh + 4u * (uint32_t)(c * A + (d ^ CFG::swz(c))),
                                     rank0 + (uint32_t)(L >> CFG::LOGCQ));
         r = ld_cluster(a);
         i = ld_cluster(a + 4u * (uint32_t)(A * CQ));
