@@ -257,7 +257,21 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         if (tid == 0) tc::bulk_wait_read0();
         if constexpr (!CFG::PREFETCH) {
             __syncthreads();
-            if (tid == 0) { load_tile(tile); x_pending = true; }
+            if (tid == 0) {
+                load_tile(tile);
+                x_pending = true;
+                // the next tile into L2 meanwhile: its copy, issued when this
+                // tile's output has left the shared region, then reads L2
+                const long long nx = tile + gridDim.x;
+                if (nx < ntiles) {
+                    const long long f2 = nx * TPT;
+                    const uint32_t b2 = (uint32_t)(((batch - f2 < TPT) ? (batch - f2) : TPT) * N * 4);
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                                 :: "l"(xr + f2 * N), "r"(b2) : "memory");
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                                 :: "l"(xi + f2 * N), "r"(b2) : "memory");
+                }
+            }
         }
         if (__syncthreads_or(!tc::mbar_wait(mb_x, ph_x))) { bad = 1; break; }
         ph_x ^= 1;
