@@ -5,8 +5,11 @@
 // banks).  The other candidates change the radix split, the threads per
 // transform, the register-DFT order (Eq. (6) order, "DIT") or, for N = 16
 // and 32, move the rows through shared memory by whole lines (k_rows_tr);
-// the autotuner times them.
+// for N = 16 .. 64 the last one spreads a transform over 2 .. 8 lanes with
+// butterflies across lanes by warp shuffles (k_rows_shfl).  The autotuner
+// times them.
 #include "kernels_rows.cuh"
+#include "rows_shfl.h"
 
 namespace sdft {
 
@@ -47,7 +50,11 @@ const KernelInfo* rows_candidate_small(int logn, int idx) {
         rows_info<RowCfg<9, 5, 5, 4, 0, 16, 16, 2>>("N=512: 16 threads/transform, radix [32,16]"),
         rows_info<RowCfg<9, 5, 5, 4, 0, 16, 16, 2, true>>("N=512: 16 threads/transform, radix [32,16], Eq. (6) order"),
         rows_info<RowCfg<9, 4, 4, 4, 1, 8, 0, 4>>("N=512: 32 threads/transform, radix [16,16,2]")};
-#define SDFT_PICK(arr) return idx < (int)(sizeof(arr) / sizeof(arr[0])) ? &arr[idx] : nullptr
+    // after a length's own candidates: the warp-shuffle form (rows_shfl.cu)
+#define SDFT_PICK(arr)                                                              \
+    return idx < (int)(sizeof(arr) / sizeof(arr[0]))                               \
+               ? &arr[idx]                                                          \
+               : rows_shfl_candidate(logn, idx - (int)(sizeof(arr) / sizeof(arr[0])))
     if (idx < 0) return nullptr;
     switch (logn) {
         case 1: SDFT_PICK(k1);
