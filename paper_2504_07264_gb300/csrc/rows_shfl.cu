@@ -167,8 +167,10 @@ KernelInfo shfl_info(const char* name) {
 
 const KernelInfo* rows_shfl_candidate(int logn, int idx) {
     // (Measured and left out: N = 8 as 2 x 4 and N = 128 as 16 x 8, no faster
-    // than the one-thread and 8-thread forms; N = 16 as 4 x 4, slower than
-    // 2 x 8; 16 points per lane, whose 64-byte lane stride halves coalescing.)
+    // than the one-thread and 8-thread forms; N = 128 as 8 lanes x two groups
+    // of 8 with a radix-2 step in registers first, 119 registers and slower;
+    // N = 16 as 4 x 4, slower than 2 x 8; 16 points per lane, whose 64-byte
+    // lane stride halves coalescing.)
     static const KernelInfo k4 = shfl_info<ShflCfg<4, 3>>(
         "N=16: 2 lanes/transform x 8 points, butterflies across lanes by warp shuffles");
     static const KernelInfo k5 = shfl_info<ShflCfg<5, 3>>(
