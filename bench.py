@@ -249,6 +249,39 @@ def _time_steps(fn, steps: int, stream) -> float:
     return start.elapsed_time(end) / steps
 
 
+def _err_sums(gr, gi, xr_rows, xi_rows):
+    """Squared error of GPU rows (gr, gi) against a float64 FFT (numpy.fft) of
+    the input rows, and the squared norm of that reference, per row."""
+    import numpy as np
+    ref = np.fft.fft(np.asarray(xr_rows, np.float64) + 1j * np.asarray(xi_rows, np.float64))
+    er = np.asarray(gr, np.float64) - ref.real
+    ei = np.asarray(gi, np.float64) - ref.imag
+    return (er ** 2 + ei ** 2).sum(-1), (ref.real ** 2 + ref.imag ** 2).sum(-1)
+
+
+def _rel_l2(num, den) -> dict:
+    """Relative L2 error over the sample and of its worst transform."""
+    import numpy as np
+    num, den = np.atleast_1d(num), np.atleast_1d(den)
+    return {"rel_l2": float(np.sqrt(num.sum() / den.sum())),
+            "worst_transform": float(np.sqrt(num / den).max())}
+
+
+def _sample_rows(plan_run, xr_h, xi_h, yr, yi, count: int, seed: int = 8) -> dict:
+    """Run `plan_run` once (it writes yr, yi) and compare `count` sampled rows
+    of a uniform batch with a float64 FFT."""
+    import numpy as np
+    import torch
+    plan_run()
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(seed).choice(xr_h.shape[0], count, replace=False))
+    sel = torch.from_numpy(idx).to(yr.device)
+    out = _rel_l2(*_err_sums(yr.index_select(0, sel).cpu().numpy(),
+                             yi.index_select(0, sel).cpu().numpy(), xr_h[idx], xi_h[idx]))
+    out["sample"] = f"{count} transforms vs a float64 FFT (numpy.fft)"
+    return out
+
+
 def _step_stats(fn, n: int, stream) -> dict:
     """Median and best of `n` individually timed steps (CUDA events around
     each call on `stream`), milliseconds."""
@@ -340,6 +373,9 @@ def run_ours(args) -> None:
             ms_sf = _time_steps(sf, split_steps, stream)
             ms_sa = _time_steps(sa, split_steps, stream)
             split_desc = splan.describe()
+            # after the timed regions: sampled accuracy of both forward paths
+            acc_split = _sample_rows(sf, xr_h, xi_h, yr, yi, 64)
+    acc_f32 = _sample_rows(fwd, xr_h, xi_h, yr, yi, 64)
     clocks = clk.summary(m0, m1 if m1 > m0 else None)
     ms_fwd = max_over_ranks(ms_fwd, dist)
     ms_adj = max_over_ranks(ms_adj, dist)
@@ -418,8 +454,9 @@ def run_ours(args) -> None:
                         "frac": BYTES_PER_POINT * points / (ms_sf * 1e-3) / 1e9 / peaks["hbm_gbs"]},
             "adjoint": {"value": points / (ms_sa * 1e-3) / 1e9, "unit": UNIT, "ms": ms_sa,
                         "frac": BYTES_PER_POINT * points / (ms_sa * 1e-3) / 1e9 / peaks["hbm_gbs"]},
-            "steps": split_steps, "schedule": split_desc,
+            "steps": split_steps, "schedule": split_desc, "accuracy": acc_split,
             "what": "rank 0's GPU, same inputs, timed after the FP32 region"},
+        "accuracy": acc_f32,
         "e2e": None if e2e_s is None else {
             "value": world * points / e2e_s / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": 2 * points * 4, "d2h_bytes_per_step": 2 * points * 4,
@@ -562,6 +599,16 @@ def run_workload(args) -> None:
             ms_a = _time_steps(adj, args.steps, stream)
             line["schedule"] = plan.describe()
             line["launches_per_call"] = plan.launches(SDFT_FORWARD)
+            # after the timed region: 64 sampled transforms against a float64 FFT
+            fwd()
+            torch.cuda.synchronize()
+            yr_h, yi_h = yr.cpu().numpy(), yi.cpu().numpy()
+            pick = np.sort(np.random.default_rng(8).choice(lengths.size, 64, replace=False))
+            sums = [_err_sums(yr_h[off[t]:off[t + 1]], yi_h[off[t]:off[t + 1]],
+                              xr_h[off[t]:off[t + 1]], xi_h[off[t]:off[t + 1]]) for t in pick]
+            line["accuracy"] = dict(_rel_l2(np.array([a for a, _ in sums]),
+                                            np.array([b for _, b in sums])),
+                                    sample="64 transforms (all lengths) vs a float64 FFT (numpy.fft)")
         for name, ms in (("forward", ms_f), ("adjoint", ms_a)):
             gbs = BYTES_PER_POINT * points / (ms * 1e-3) / 1e9
             line[name] = {"gpts": points / (ms * 1e-3) / 1e9, "ms": ms, "gbs": gbs,
