@@ -50,8 +50,9 @@ BYTES_PER_POINT = 16          # algorithmic: 4 B each of xr, xi read and yr, yi 
 HEADLINE_SOURCES = ("fft_core.cuh", "kernels_rows.cuh", "rows_1024.cu", "launch.h")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one forward
-# launch of the full 65536 x 1024 workload, from one ncu capture
-# (profiles/fwd_n1024_bandwidth.md), with the source hash it was taken on.
+# launch of the full 65536 x 1024 workload, from one ncu capture of the
+# headline command (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
+# -k regex:k_rows`), with the source hash of the kernel it was taken on.
 NCU_TRAFFIC = {
     "fwd": {"bytes": 536917504 + 485014784, "hash": "b2f369da6465f460",
             "schedule": "N=1024: 32 threads/transform, radix [32,32]"},
@@ -405,6 +406,25 @@ def run_ours(args) -> None:
     describe = plan.describe()
     plan.destroy()
 
+    # The other measured configurations, on rank 0's GPU after every timed
+    # region of the headline (each with its own warm-up and CUDA-event
+    # timing; none of it is in `value`): the differentiation, precision and
+    # batching workloads, each against the plain FP32 kernel on this GPU.
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        del xr, xi, yr, yi
+        torch.cuda.empty_cache()
+        xsteps = max(10, min(args.steps, 50))
+        xwarm = max(3, min(args.warmup, 5))
+        with ClockSampler(gpu_id) as xclk:
+            extra["autograd"] = autograd_block(xsteps, xwarm, stream)
+            torch.cuda.empty_cache()
+            extra["precision"] = precision_block(xsteps, xwarm, stream, with_n1024=False)
+            torch.cuda.empty_cache()
+            extra["ragged"] = ragged_block(xsteps, xwarm, stream)
+            torch.cuda.empty_cache()
+        extra["extra_clocks"] = xclk.summary()
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -468,6 +488,7 @@ def run_ours(args) -> None:
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "kernel_source_hash": src_hash,
+        **extra,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -523,9 +544,148 @@ def _measure_uniform(n: int, batch: int, xr_h, xi_h, steps: int, warmup: int, st
     return out
 
 
+def autograd_block(steps: int, warmup: int, stream) -> dict:
+    """The differentiation workload: N = 4096, batch 16384, iid N(0,1) seed 1;
+    forward and adjoint kernels, and the whole autograd step (split_dft,
+    loss sum(w_r yr^2 + w_i yi^2) with w iid U[0,1) seed 2, backward)."""
+    import torch
+
+    import workloads
+    from paper_2504_07264_gb300 import split_dft
+    cfg = workloads.AUTOGRAD
+    n, batch = cfg["n"], cfg["batch"]
+    xr_h, xi_h = workloads.normal_planes(n, batch, cfg["seed"])
+    out = _measure_uniform(n, batch, xr_h, xi_h, steps, warmup, stream, accuracy_sample=32)
+    wr_h, wi_h = workloads.loss_weights(n, batch, cfg["weight_seed"])
+    xr = torch.from_numpy(xr_h).cuda().requires_grad_(True)
+    xi = torch.from_numpy(xi_h).cuda().requires_grad_(True)
+    wr, wi = torch.from_numpy(wr_h).cuda(), torch.from_numpy(wi_h).cuda()
+
+    def step():
+        xr.grad = None
+        xi.grad = None
+        yr, yi = split_dft(xr, xi)
+        (wr * yr ** 2 + wi * yi ** 2).sum().backward()
+    for _ in range(warmup):
+        step()
+    ms = _time_steps(step, max(5, steps // 10), stream)
+    out["autograd_step"] = {"ms": ms, "gpts": n * batch / (ms * 1e-3) / 1e9,
+                            "what": "split_dft forward + weighted-square loss + backward "
+                                    "(adjoint kernel), torch elementwise ops included"}
+    out["workload"] = (f"differentiation: N={n} x {batch} FP32 planar, iid N(0,1) seed 1; "
+                       "loss weights U[0,1) seed 2")
+    return out
+
+
+def precision_block(steps: int, warmup: int, stream, with_n1024: bool = True) -> dict:
+    """The precision workload: N = 256, batch 262144, |x| = 10^U(-3,3) with
+    uniform phase (seed 3), on the FP32 kernel and on the split-BF16 and
+    split-FP16 tensor-core paths, each with its error on 256 sampled
+    transforms; optionally the same three paths on the N = 1024 x 65536
+    bandwidth workload."""
+    import workloads
+    cfg = workloads.PRECISION
+    n, batch = cfg["n"], cfg["batch"]
+    xr_h, xi_h = workloads.precision()
+    paths = {}
+    for name, dt in (("f32", 0), ("split_bf16", 1), ("split_fp16", 2)):
+        paths[name] = _measure_uniform(n, batch, xr_h, xi_h, steps, warmup, stream,
+                                       dtype=dt, accuracy_sample=256)
+    del xr_h, xi_h
+    if with_n1024:
+        br, bi = workloads.bandwidth()
+        for name, dt in (("f32_n1024", 0), ("split_bf16_n1024", 1), ("split_fp16_n1024", 2)):
+            paths[name] = _measure_uniform(1024, 65536, br, bi, steps, warmup, stream,
+                                           dtype=dt, accuracy_sample=64)
+    for name in ("split_bf16", "split_fp16"):
+        paths[name]["vs_f32_forward"] = paths[name]["forward"]["gpts"] / paths["f32"]["forward"]["gpts"]
+    return {"paths": paths,
+            "workload": (f"precision: N={n} x {batch}, |x| = 10^U(-3,3), phase U[0,2pi), seed 3; "
+                         "FP32 kernel vs split-BF16 vs split-FP16 tensor cores")}
+
+
+def ragged_block(steps: int, warmup: int, stream, tune: bool = True) -> dict:
+    """The batching workload: 10000 transforms of lengths 2^k, k uniform in
+    {3..16} (seed 4), iid N(0,1): one persistent launch per call replayed from
+    a CUDA graph (forward and adjoint), the plan's tuner run first; the same
+    transforms as one uniform FP32 plan per length for comparison."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2504_07264_gb300 import SDFT_ADJOINT, SDFT_FORWARD, Plan
+    peak = _peaks()["hbm_gbs"]
+    lengths, off, xr_h, xi_h = workloads.ragged_planes()
+    points = int(off[-1])
+    xr = torch.from_numpy(xr_h).cuda()
+    xi = torch.from_numpy(xi_h).cuda()
+    yr = torch.empty_like(xr)
+    yi = torch.empty_like(xi)
+    line = {}
+    with Plan(lengths=lengths) as plan:
+        if tune:
+            # each length's schedule, chosen on this batch by the plan's tuner
+            line["ragged_tuning"] = plan.ragged_autotune(xr, xi, yr, yi, reps=5, stream=stream)
+        fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
+        adj = lambda: plan.execute(SDFT_ADJOINT, xr, xi, yr, yi, stream)  # noqa: E731
+        for _ in range(warmup):
+            fwd()
+            adj()
+        torch.cuda.synchronize()
+        ms_f = _time_steps(fwd, steps, stream)
+        ms_a = _time_steps(adj, steps, stream)
+        line["schedule"] = plan.describe()
+        line["launches_per_call"] = plan.launches(SDFT_FORWARD)
+        # after the timed region: 64 sampled transforms against a float64 FFT
+        fwd()
+        torch.cuda.synchronize()
+        yr_h, yi_h = yr.cpu().numpy(), yi.cpu().numpy()
+        pick = np.sort(np.random.default_rng(8).choice(lengths.size, 64, replace=False))
+        sums = [_err_sums(yr_h[off[t]:off[t + 1]], yi_h[off[t]:off[t + 1]],
+                          xr_h[off[t]:off[t + 1]], xi_h[off[t]:off[t + 1]]) for t in pick]
+        line["accuracy"] = dict(_rel_l2(np.array([a for a, _ in sums]),
+                                        np.array([b for _, b in sums])),
+                                sample="64 transforms (all lengths) vs a float64 FFT (numpy.fft)")
+    for name, ms in (("forward", ms_f), ("adjoint", ms_a)):
+        gbs = BYTES_PER_POINT * points / (ms * 1e-3) / 1e9
+        line[name] = {"gpts": points / (ms * 1e-3) / 1e9, "ms": ms, "gbs": gbs,
+                      "frac": gbs / peak}
+    del xr, xi, yr, yi
+    # the same transforms as one uniform plan per length (one launch each),
+    # on per-length contiguous copies of the data
+    plans, bufs = [], []
+    for logn in range(2, 17):
+        sel = np.nonzero(lengths == (1 << logn))[0]
+        if sel.size == 0:
+            continue
+        rows_r = np.concatenate([xr_h[off[t]:off[t + 1]] for t in sel])
+        rows_i = np.concatenate([xi_h[off[t]:off[t + 1]] for t in sel])
+        a = torch.from_numpy(rows_r).cuda()
+        b = torch.from_numpy(rows_i).cuda()
+        bufs.append((a, b, torch.empty_like(a), torch.empty_like(b)))
+        plans.append(Plan(1 << logn, int(sel.size)))
+
+    def per_length():
+        for pl, (a, b, c, d) in zip(plans, bufs):
+            pl.execute(SDFT_FORWARD, a, b, c, d, stream)
+    for _ in range(warmup):
+        per_length()
+    ms_u = _time_steps(per_length, steps, stream)
+    for pl in plans:
+        pl.destroy()
+    gbs = BYTES_PER_POINT * points / (ms_u * 1e-3) / 1e9
+    line["per_length_uniform_kernels"] = {
+        "gpts": points / (ms_u * 1e-3) / 1e9, "ms": ms_u, "gbs": gbs, "frac": gbs / peak,
+        "launches": len(plans), "what": "one uniform FP32 plan per length, data pre-sorted"}
+    line["vs_per_length_uniform"] = line["forward"]["gpts"] / line["per_length_uniform_kernels"]["gpts"]
+    line["points"] = points
+    line["workload"] = (f"batching: {lengths.size} transforms, lengths 2^U{{3..16}} (seed 4), "
+                        f"{points} points, iid N(0,1); one persistent launch in a CUDA graph")
+    return line
+
+
 def run_workload(args) -> None:
     """Single-GPU measurements of the other configurations (one JSON line)."""
-    import numpy as np
     import torch
 
     import workloads
@@ -537,109 +697,16 @@ def run_workload(args) -> None:
     line = {"workload": args.workload, "unit": UNIT, "peak_gbs": peak, "steps": args.steps,
             "warmup": args.warmup}
     if args.workload == "autograd":
-        from paper_2504_07264_gb300 import split_dft
-        cfg = workloads.AUTOGRAD
-        n, batch = cfg["n"], cfg["batch"]
-        xr_h, xi_h = workloads.normal_planes(n, batch, cfg["seed"])
-        line.update(_measure_uniform(n, batch, xr_h, xi_h, args.steps, args.warmup, stream))
-        wr_h, wi_h = workloads.loss_weights(n, batch, cfg["weight_seed"])
-        xr = torch.from_numpy(xr_h).cuda().requires_grad_(True)
-        xi = torch.from_numpy(xi_h).cuda().requires_grad_(True)
-        wr, wi = torch.from_numpy(wr_h).cuda(), torch.from_numpy(wi_h).cuda()
-
-        def step():
-            xr.grad = None
-            xi.grad = None
-            yr, yi = split_dft(xr, xi)
-            (wr * yr ** 2 + wi * yi ** 2).sum().backward()
-        for _ in range(args.warmup):
-            step()
-        ms = _time_steps(step, max(5, args.steps // 10), stream)
-        line["autograd_step"] = {"ms": ms, "gpts": n * batch / (ms * 1e-3) / 1e9,
-                                 "what": "split_dft forward + weighted-square loss + backward "
-                                         "(adjoint kernel), torch elementwise ops included"}
+        line.update(autograd_block(args.steps, args.warmup, stream))
         line["metric"] = "planar DFT Gpts/s, N=4096 B=16384, fwd + adj kernels and autograd step"
         line["value"] = line["forward"]["gpts"]
     elif args.workload == "precision":
-        cfg = workloads.PRECISION
-        n, batch = cfg["n"], cfg["batch"]
-        xr_h, xi_h = workloads.precision()
-        paths = {}
-        for name, dt in (("f32", 0), ("split_bf16", 1), ("split_fp16", 2)):
-            paths[name] = _measure_uniform(n, batch, xr_h, xi_h, args.steps, args.warmup, stream,
-                                           dtype=dt, accuracy_sample=256)
-        del xr_h, xi_h
-        # the bandwidth workload's shape on the split-BF16 path as well
-        br, bi = workloads.bandwidth()
-        for name, dt in (("f32_n1024", 0), ("split_bf16_n1024", 1), ("split_fp16_n1024", 2)):
-            paths[name] = _measure_uniform(1024, 65536, br, bi, args.steps, args.warmup, stream,
-                                           dtype=dt, accuracy_sample=64)
-        line["paths"] = paths
+        line.update(precision_block(args.steps, args.warmup, stream))
         line["metric"] = ("planar DFT Gpts/s, N=256 B=262144 |x| log-uniform: FP32 vs split-BF16 vs "
                           "split-FP16 tensor cores (and N=1024 B=65536)")
-        line["value"] = paths["split_bf16"]["forward"]["gpts"]
+        line["value"] = line["paths"]["split_bf16"]["forward"]["gpts"]
     elif args.workload == "ragged":
-        from paper_2504_07264_gb300 import SDFT_ADJOINT, SDFT_FORWARD, Plan
-        lengths, off, xr_h, xi_h = workloads.ragged_planes()
-        points = int(off[-1])
-        xr = torch.from_numpy(xr_h).cuda()
-        xi = torch.from_numpy(xi_h).cuda()
-        yr = torch.empty_like(xr)
-        yi = torch.empty_like(xi)
-        with Plan(lengths=lengths) as plan:
-            # each length's routine form, chosen on this batch by the plan's tuner
-            line["ragged_variants"] = plan.ragged_autotune(xr, xi, yr, yi, reps=5, stream=stream)
-            fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
-            adj = lambda: plan.execute(SDFT_ADJOINT, xr, xi, yr, yi, stream)  # noqa: E731
-            for _ in range(args.warmup):
-                fwd()
-                adj()
-            torch.cuda.synchronize()
-            ms_f = _time_steps(fwd, args.steps, stream)
-            ms_a = _time_steps(adj, args.steps, stream)
-            line["schedule"] = plan.describe()
-            line["launches_per_call"] = plan.launches(SDFT_FORWARD)
-            # after the timed region: 64 sampled transforms against a float64 FFT
-            fwd()
-            torch.cuda.synchronize()
-            yr_h, yi_h = yr.cpu().numpy(), yi.cpu().numpy()
-            pick = np.sort(np.random.default_rng(8).choice(lengths.size, 64, replace=False))
-            sums = [_err_sums(yr_h[off[t]:off[t + 1]], yi_h[off[t]:off[t + 1]],
-                              xr_h[off[t]:off[t + 1]], xi_h[off[t]:off[t + 1]]) for t in pick]
-            line["accuracy"] = dict(_rel_l2(np.array([a for a, _ in sums]),
-                                            np.array([b for _, b in sums])),
-                                    sample="64 transforms (all lengths) vs a float64 FFT (numpy.fft)")
-        for name, ms in (("forward", ms_f), ("adjoint", ms_a)):
-            gbs = BYTES_PER_POINT * points / (ms * 1e-3) / 1e9
-            line[name] = {"gpts": points / (ms * 1e-3) / 1e9, "ms": ms, "gbs": gbs,
-                          "frac": gbs / peak}
-        # the same transforms as one uniform plan per length (one launch each),
-        # on per-length contiguous copies of the data
-        plans, bufs = [], []
-        for logn in range(2, 17):
-            sel = np.nonzero(lengths == (1 << logn))[0]
-            if sel.size == 0:
-                continue
-            rows_r = np.concatenate([xr_h[off[t]:off[t + 1]] for t in sel])
-            rows_i = np.concatenate([xi_h[off[t]:off[t + 1]] for t in sel])
-            a = torch.from_numpy(rows_r).cuda()
-            b = torch.from_numpy(rows_i).cuda()
-            bufs.append((a, b, torch.empty_like(a), torch.empty_like(b)))
-            plans.append(Plan(1 << logn, int(sel.size)))
-
-        def per_length():
-            for pl, (a, b, c, d) in zip(plans, bufs):
-                pl.execute(SDFT_FORWARD, a, b, c, d, stream)
-        for _ in range(args.warmup):
-            per_length()
-        ms_u = _time_steps(per_length, args.steps, stream)
-        for pl in plans:
-            pl.destroy()
-        gbs = BYTES_PER_POINT * points / (ms_u * 1e-3) / 1e9
-        line["per_length_uniform_kernels"] = {
-            "gpts": points / (ms_u * 1e-3) / 1e9, "ms": ms_u, "gbs": gbs, "frac": gbs / peak,
-            "launches": len(plans), "what": "one uniform FP32 plan per length, data pre-sorted"}
-        line["points"] = points
+        line.update(ragged_block(args.steps, args.warmup, stream))
         line["metric"] = ("planar DFT Gpts/s, ragged batch of 10000 transforms, lengths 2^U{3..16} "
                           "(seed 4), one persistent launch in a CUDA graph")
         line["value"] = line["forward"]["gpts"]
@@ -716,6 +783,9 @@ def main(argv=None) -> int:
                     help="skip the CPU oracle timing (it is on by default)")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the host-buffer end-to-end leg (it is on by default)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the differentiation, precision and batching configurations "
+                         "measured after the headline (they are on by default)")
     ap.add_argument("--workload",
                     choices=("bandwidth", "autograd", "precision", "ragged", "sizes", "uniform",
                              "plain"),

@@ -18,8 +18,17 @@ _plans: dict[tuple, Plan] = {}
 
 
 def get_plan(n: int, batch: int, device: torch.device, dtype: int = SDFT_F32) -> Plan:
-    """A cached plan for (n, batch) on ``device``."""
-    key = (int(n), int(batch), int(dtype), device.index)
+    """A cached plan for (n, batch) on ``device`` and the current stream.
+
+    A plan's device-side state (its status word; on the work-queue and
+    two-pass schedules of long transforms, a work counter or a scratch area)
+    is shared by every call on it, so calls that overlap on the GPU must not
+    share a plan.  The cache is therefore keyed on the current CUDA stream as
+    well: work issued from different streams gets different plans, and calls
+    on one stream are ordered by that stream.
+    """
+    stream = torch.cuda.current_stream(device).cuda_stream
+    key = (int(n), int(batch), int(dtype), device.index, int(stream))
     with _cache_lock:
         p = _plans.get(key)
         if p is None:

@@ -715,20 +715,34 @@ int sdft_execute_host(sdft_plan* plan, int direction, const float* xr, const flo
                             : std::max<int64_t>(1, ((int64_t)32 << 20) / (n * (int64_t)sizeof(float)));
         chunk = std::min<int64_t>(chunk, plan->batch);
         const int64_t chunk_points = rag ? plan->points : chunk * n;
+        // Each resource is created only if an earlier, failed set-up has not
+        // already made it, so a retry completes the set-up instead of leaking
+        // (the sizes depend on the plan alone); the plan frees them all.
         for (int sl = 0; sl < 2; ++sl) {
             for (int pl = 0; pl < 2; ++pl)
-                if (cudaMalloc(&h.d_buf[sl][pl], (size_t)chunk_points * sizeof(float)) != cudaSuccess)
+                if (!h.d_buf[sl][pl] &&
+                    cudaMalloc(&h.d_buf[sl][pl], (size_t)chunk_points * sizeof(float)) != cudaSuccess) {
+                    h.d_buf[sl][pl] = nullptr;
                     return fail(SDFT_ERR_ALLOC);
-            if (cudaStreamCreateWithFlags(&h.streams[sl], cudaStreamNonBlocking) != cudaSuccess)
+                }
+            if (!h.streams[sl] &&
+                cudaStreamCreateWithFlags(&h.streams[sl], cudaStreamNonBlocking) != cudaSuccess) {
+                h.streams[sl] = nullptr;
                 return fail(SDFT_ERR_CUDA);
+            }
         }
-        if (cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming) != cudaSuccess)
+        if (!h.start && cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming) != cudaSuccess) {
+            h.start = nullptr;
             return fail(SDFT_ERR_CUDA);
+        }
         // a work-queue plan moves its batch as one chunk (slot 0 only)
         const int64_t scr = rag ? 0 : plan->kern->scratch_per_cta;
-        if (scr > 0) {
+        if (scr > 0 && !h.d_scratch) {
             const size_t sb = (size_t)plan->grid * (size_t)scr * sizeof(float2);
-            if (cudaMalloc(&h.d_scratch, sb) != cudaSuccess) return fail(SDFT_ERR_ALLOC);
+            if (cudaMalloc(&h.d_scratch, sb) != cudaSuccess) {
+                h.d_scratch = nullptr;
+                return fail(SDFT_ERR_ALLOC);
+            }
         }
         h.chunk = chunk;
     }

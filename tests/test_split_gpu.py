@@ -27,12 +27,15 @@ def _cuda():
     O.build()
 
 
-def _run(xr, xi, dtype, direction=0):
+def _run(xr, xi, dtype, direction=0, grid=None):
     import torch
 
     from paper_2504_07264_gb300 import Plan
     batch, n = xr.shape
     with Plan(n, batch, dtype) as plan:
+        if grid is not None:
+            plan.set_grid(grid)
+            assert plan.grid == grid
         yr, yi = plan.execute(direction, torch.from_numpy(xr).cuda(), torch.from_numpy(xi).cuda())
         torch.cuda.synchronize()
         status = plan.sync_status()
@@ -57,6 +60,63 @@ def test_split_matches_oracle(n, dt, direction):
     g = _global_rel(yr, yi, rr, ri)
     worst = rel_l2_rows(yr, yi, rr, ri).max()
     assert g <= TOL_SPLIT, f"{dt} N={n}: global rel L2 {g:.3e} (worst transform {worst:.3e})"
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+@pytest.mark.parametrize("dt", sorted(DTYPES))
+@pytest.mark.parametrize("direction", [0, 1])
+@pytest.mark.parametrize("grid", [1, 4])
+def test_split_several_tiles_per_cta(n, dt, direction, grid):
+    """A small grid, so that every CTA runs at least three tiles of 128 GEMM
+    rows (128/R transforms each) and the last tile is partial: the persistent
+    tile loop -- operand-region reuse after the output copy, the next tile's
+    prefetch, the mbarrier phases carried from tile to tile -- against the
+    float64 oracle, transform by transform."""
+    tpt = 128 // int(round(n ** 0.5))              # transforms per tile (R = sqrt(N))
+    batch = 3 * grid * tpt + 1
+    xr, xi = W.logmag_phase_planes(n, batch, seed=30 + n % 7 + 2 * direction + grid)
+    yr, yi = _run(xr, xi, DTYPES[dt], direction, grid=grid)
+    fn = O.dft_factored_dit if direction == 0 else O.adjoint_factored
+    rr, ri = fn(xr, xi)
+    g = _global_rel(yr, yi, rr, ri)
+    rows = rel_l2_rows(yr, yi, rr, ri)
+    worst = int(np.argmax(rows))
+    assert np.isfinite(yr).all() and np.isfinite(yi).all()
+    assert g <= TOL_SPLIT, (f"{dt} N={n} grid {grid}: global rel L2 {g:.3e} "
+                            f"(worst transform {worst}: {rows[worst]:.3e})")
+    # every transform, the partial last tile's included, carries the bound too
+    assert rows.max() <= 4 * TOL_SPLIT, f"transform {worst}: {rows[worst]:.3e}"
+
+
+@pytest.mark.parametrize("dt", sorted(DTYPES))
+@pytest.mark.parametrize("direction", [0, 1])
+def test_split_full_size_bandwidth_config(dt, direction):
+    """N = 1024, batch 65536 (iid N(0,1), seed 1): the benchmark's split
+    plan and grid.  128 sampled transforms against the float64 oracle,
+    Parseval (forward) or its adjoint form on every transform."""
+    import torch
+
+    from paper_2504_07264_gb300 import Plan
+    xr, xi = W.bandwidth()
+    n, batch = W.BANDWIDTH["n"], W.BANDWIDTH["batch"]
+    with Plan(n, batch, DTYPES[dt]) as plan:
+        dxr = torch.from_numpy(xr).cuda()
+        dxi = torch.from_numpy(xi).cuda()
+        yr, yi = plan.execute(direction, dxr, dxi)
+        e_in = (dxr.double() ** 2 + dxi.double() ** 2).sum(1) * n
+        e_out = (yr.double() ** 2 + yi.double() ** 2).sum(1)
+        parseval = ((e_out - e_in).abs() / e_in).max().item()
+        idx = np.sort(np.random.default_rng(11 + direction).choice(batch, 128, replace=False))
+        sel = torch.from_numpy(idx).cuda()
+        gr = yr.index_select(0, sel).cpu().numpy()
+        gi = yi.index_select(0, sel).cpu().numpy()
+        assert plan.sync_status() == 0
+    fn = O.dft_factored_dit if direction == 0 else O.adjoint_factored
+    rr, ri = fn(xr[idx], xi[idx])
+    rows = rel_l2_rows(gr, gi, rr, ri)
+    g = _global_rel(gr, gi, rr, ri)
+    assert g <= TOL_SPLIT, f"{dt}: global rel L2 {g:.3e} (worst transform {rows.max():.3e})"
+    assert parseval < 1e-4
 
 
 @pytest.mark.parametrize("dt", sorted(DTYPES))

@@ -3,15 +3,17 @@
 sdft_execute_noalloc serves callers that cannot allocate device memory: it
 runs the N = 32768 / 65536 kernel on scratch and twiddle tables held in
 file-scope device arrays instead of plan-owned cudaMalloc memory.  Its results
-must match the plan-based entry point, on two calls in a row (the second call
-reuses the arrays the first one left behind).  This file is collected last so
-that a run stopping at its first failure has already run every other test.
+must match the float64 oracle, on two calls in a row (the second call reuses
+the arrays the first one left behind), out of place and in place.  This file
+is collected last so that a run stopping at its first failure has already run
+every other test.
 """
 import numpy as np
 import pytest
 
 import workloads as W
 from gpu_util import TOL_F32, rel_l2_rows
+from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -22,22 +24,28 @@ def _cuda():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     from paper_2504_07264_gb300 import build
     build.build()
+    O.build()
 
 
+def _oracle(direction, xr, xi):
+    fn = O.dft_factored_dit if direction == 0 else O.adjoint_factored
+    return fn(xr, xi)
+
+
+# batches above the slot count (32 at N = 32768, 16 at N = 65536), so that the
+# CTAs take transforms in turn and reuse their scratch slots
 @pytest.mark.parametrize("n,batch", [(32768, 37), (65536, 19)])
 @pytest.mark.parametrize("direction", [0, 1])
-def test_noalloc_matches_plan_entry_point(n, batch, direction):
+def test_noalloc_matches_oracle(n, batch, direction):
+    """Two calls in a row through the C ABI against the float64 oracle; the
+    second call runs on the scratch the first one left behind."""
     import torch
 
-    from paper_2504_07264_gb300 import Plan
     from paper_2504_07264_gb300 import sdft as S
     xr, xi = W.normal_planes(n, batch, seed=700 + n % 97 + direction)
+    ref_r, ref_i = _oracle(direction, xr, xi)
     dxr = torch.from_numpy(xr).cuda()
     dxi = torch.from_numpy(xi).cuda()
-    with Plan(n, batch) as plan:
-        rr, ri = plan.execute(direction, dxr, dxi)
-    ref_r = rr.cpu().numpy().astype(np.float64)
-    ref_i = ri.cpu().numpy().astype(np.float64)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         yr = torch.full_like(dxr, float("nan"))
@@ -48,6 +56,36 @@ def test_noalloc_matches_plan_entry_point(n, batch, direction):
         torch.cuda.synchronize()
         err = rel_l2_rows(yr.cpu().numpy(), yi.cpu().numpy(), ref_r, ref_i)
         assert err.max() <= TOL_F32, f"call {call}: max rel err {err.max():.3e}"
+
+
+@pytest.mark.parametrize("n,batch", [(32768, 37), (65536, 19)])
+def test_noalloc_in_place(n, batch):
+    """In place (yr == xr, yi == xi), forward then adjoint, each against the
+    oracle; the second call transforms the first one's output in place."""
+    import torch
+
+    from paper_2504_07264_gb300 import sdft as S
+    xr, xi = W.normal_planes(n, batch, seed=750 + n % 89)
+    fr, fi = _oracle(0, xr, xi)
+    dr = torch.from_numpy(xr).cuda()
+    di = torch.from_numpy(xi).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    st = S.sdft_execute_noalloc(n, batch, 0, dr.data_ptr(), di.data_ptr(), dr.data_ptr(),
+                                di.data_ptr(), stream)
+    assert st == S.SDFT_OK, S.sdft_status_string(st)
+    torch.cuda.synchronize()
+    gr, gi = dr.cpu().numpy(), di.cpu().numpy()
+    err = rel_l2_rows(gr, gi, fr, fi)
+    assert err.max() <= TOL_F32, f"forward in place: max rel err {err.max():.3e}"
+    # adjoint of the GPU's own forward result, in place, against the oracle's
+    # adjoint of those same float32 values
+    ar, ai = _oracle(1, gr, gi)
+    st = S.sdft_execute_noalloc(n, batch, 1, dr.data_ptr(), di.data_ptr(), dr.data_ptr(),
+                                di.data_ptr(), stream)
+    assert st == S.SDFT_OK, S.sdft_status_string(st)
+    torch.cuda.synchronize()
+    err = rel_l2_rows(dr.cpu().numpy(), di.cpu().numpy(), ar, ai)
+    assert err.max() <= TOL_F32, f"adjoint in place: max rel err {err.max():.3e}"
 
 
 def test_noalloc_rejects_other_lengths():
