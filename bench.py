@@ -624,8 +624,10 @@ def ragged_block(steps: int, warmup: int, stream, tune: bool = True) -> dict:
     line = {}
     with Plan(lengths=lengths) as plan:
         if tune:
-            # each length's schedule, chosen on this batch by the plan's tuner
+            # each length's form, chosen on this batch by the plan's tuner
             line["ragged_tuning"] = plan.ragged_autotune(xr, xi, yr, yi, reps=5, stream=stream)
+        line["forms"] = {str(1 << l): plan.ragged_form(1 << l)
+                         for l in range(2, 17) if (lengths == (1 << l)).any()}
         fwd = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
         adj = lambda: plan.execute(SDFT_ADJOINT, xr, xi, yr, yi, stream)  # noqa: E731
         for _ in range(warmup):

@@ -98,9 +98,12 @@ SDFT_API sdft_plan* sdft_plan_create(int64_t n, int64_t batch, int dtype);
  * power of two in [4, 65536].  Rows are concatenated in the order given.
  * Forward and adjoint calls on such a plan run as one persistent kernel
  * launch (thread-block clusters of 8 CTAs, replayed from a CUDA graph) that
- * claims work from a device queue, largest transforms first: a transform of
- * N >= 16384 is held in the shared memory of N / 8192 CTAs of a cluster,
- * shorter ones run as tiles of one CTA.
+ * claims work from device queues, largest transforms first.  Every length
+ * runs one of its compiled forms (see sdft_ragged_form_count): a transform of
+ * N >= 8192 may be held in the distributed shared memory of 8, 4 or 2 CTAs,
+ * a shorter one (and N = 8192 in its row form) runs in a tile of one CTA.  The
+ * plan starts with the forms selected by sdft_ragged_form_select (form 0 if
+ * none) and allocates the twiddle tables of every form of its lengths.
  * Returns NULL on error (see sdft_last_error). */
 SDFT_API sdft_plan* sdft_plan_create_ragged(const int64_t* lengths, int64_t count, int dtype);
 
@@ -153,34 +156,60 @@ SDFT_API int sdft_plan_set_grid(sdft_plan* plan, int grid);
 SDFT_API int sdft_plan_grid(const sdft_plan* plan);
 
 /* Bound of the device-side waits of a work-queue plan (ragged plans, and
- * uniform plans on a work-queue schedule).  Their kernel needs no waits to
- * compute; the only ones are those added by the testing hook below.  Every
- * such wait polls at most `polls` times (~128 ns each; default 2^23, about a
- * second); past that the kernel records SDFT_ERR_TIMEOUT in the status word,
- * stops waiting anywhere and carries on.  The status stays set, and later
+ * uniform plans on a work-queue schedule): the barriers of the groups of 4
+ * and 2 CTAs that share a transform, and the wait added by the testing hook
+ * below.  Every such wait polls at most `polls` times (default 2^23); past
+ * that the kernel records SDFT_ERR_TIMEOUT in the status word, stops waiting
+ * anywhere and carries on (the results of that call are then undefined).  The status stays set, and later
  * calls skip their waits too, until sdft_plan_sync_status reads and clears it.
  * SDFT_ERR_INVALID_ARG for other plans or polls < 1. */
 SDFT_API int sdft_plan_set_wait_limit(sdft_plan* plan, int polls);
-/* Testing hook: make every long-transform item (N >= 16384) of a work-queue
- * plan first wait for a device word that nothing sets (on != 0), or not
- * (on == 0), so that the bounded-wait path can be exercised without any
- * fault on the GPU.  SDFT_ERR_INVALID_ARG for plans without long transforms. */
+/* Testing hook: make every transform a work-queue plan holds in the shared
+ * memory of several CTAs first wait for a device word that nothing sets
+ * (on != 0), or not (on == 0), so that the bounded-wait path can be exercised
+ * without any fault on the GPU.  SDFT_ERR_INVALID_ARG for plans with no such
+ * transform under their current forms. */
 SDFT_API int sdft_plan_inject_unreachable_wait(sdft_plan* plan, int on);
 
-/* Ragged plans: the row-tile routine of each length N = 32 .. 8192 comes in
- * two compiled forms, the register DFTs in decimation-in-frequency order
- * (default) or in the order of Eq. (6).  Bit l of `mask` selects the second
- * form for N = 2^l (bits 5 .. 13 only; SDFT_ERR_INVALID_ARG otherwise, or for
- * uniform plans).  The results agree within rounding. */
-SDFT_API int sdft_plan_set_ragged_variants(sdft_plan* plan, unsigned mask);
-/* The current mask (>= 0), or -status. */
-SDFT_API int sdft_plan_ragged_variants(const sdft_plan* plan);
-/* Time the plan's forward call on the caller's device buffers (the plan's
- * layout, read xr/xi, written yr/yi) with each length's form, one length at a
- * time, longest first, keeping the Eq. (6) form only where it is faster by
- * more than 1 %; `reps` timed calls per trial after one untimed call, with
- * CUDA events on `stream` (synchronises it).  Leaves the chosen mask set and
- * returns it (>= 0), or -status. */
+/* ---- forms of the work-queue kernel (ragged plans) ----------------------
+ * Each length N = 4 .. 65536 has one or more compiled forms in the persistent
+ * kernel of ragged plans: the radix split, values per thread and transforms
+ * per tile of a one-CTA row tile, or the number of CTAs (8, 4, 2) whose shared
+ * memory holds one transform of N >= 8192.  Every form computes the same
+ * transform (results agree within rounding).  Functions returning a count or
+ * index return a negative status on error. */
+/* Number of forms of length n (SDFT_ERR_UNSUPPORTED_N outside 4 .. 65536). */
+SDFT_API int sdft_ragged_form_count(int64_t n);
+/* Describe form `form` of length n into buf (snprintf convention). */
+SDFT_API int sdft_ragged_form_describe(int64_t n, int form, char* buf, int64_t len);
+/* Process-wide choice of the form of length n for work-queue plans created
+ * later (SDFT_OK, or SDFT_ERR_INVALID_ARG / SDFT_ERR_UNSUPPORTED_N). */
+SDFT_API int sdft_ragged_form_select(int64_t n, int form);
+SDFT_API int sdft_ragged_form_selected(int64_t n);
+/* Run length n of a work-queue plan (ragged plans, and uniform plans on a
+ * work-queue schedule) in form `form`: rebuilds the plan's work items and
+ * synchronises the device.  No work using the plan may be in flight.
+ * SDFT_ERR_INVALID_ARG for other plans, lengths the plan does not hold, or an
+ * unknown form. */
+SDFT_API int sdft_plan_set_ragged_form(sdft_plan* plan, int64_t n, int form);
+/* The form length n runs in on this plan (>= 0), or -status. */
+SDFT_API int sdft_plan_ragged_form(const sdft_plan* plan, int64_t n);
+/* How the groups of 4 and of 2 CTAs (phases 1 and 2) synchronise: with bit p
+ * of `mask` set, the 8 / q transforms that the groups of one cluster run at a
+ * time share the hardware cluster barrier (a group without a transform waits
+ * with the others); with it clear, every group synchronises alone through
+ * mbarriers that its CTAs arrive on remotely.  Default 0x6 (both coupled).
+ * SDFT_ERR_INVALID_ARG for other plans or bits outside 0x6. */
+SDFT_API int sdft_plan_set_ragged_coupling(sdft_plan* plan, unsigned mask);
+SDFT_API int sdft_plan_ragged_coupling(const sdft_plan* plan);
+/* Autotune a work-queue plan on the caller's device buffers (the plan's
+ * layout, read xr/xi, written yr/yi): one length at a time, longest first,
+ * time the plan's forward call with each form of that length (`reps` timed
+ * calls per trial after one untimed call, CUDA events on `stream`) and keep
+ * another form only where it is faster by more than 1 %.  Rebuilds the work
+ * items between trials, so it synchronises the device.  Leaves the chosen
+ * forms set and returns a mask with bit l set for every length 2^l that runs
+ * a form other than form 0 (>= 0), or -status. */
 SDFT_API int sdft_plan_ragged_autotune(sdft_plan* plan, const float* xr, const float* xi,
                                        float* yr, float* yi, int reps, void* stream);
 

@@ -7,14 +7,19 @@ events, the caller's buffers) and records the fastest; ``apply`` selects the
 recorded schedules for the plans created afterwards.  Results are kept as JSON
 keyed by GPU name, dtype and N:
 
-    {"NVIDIA GB300": {"0": {"1024": {"index": 0, "ms": [...], "schedules": [...]}}}}
+    {"NVIDIA GB300": {"0": {"1024": {"index": 0, "ms": [...], "schedules": [...]}},
+                      "ragged": {"32768": 1, ...}}}
+
+The "ragged" entry holds the form of every length in the persistent kernel of
+ragged plans (``tune_ragged``: the plan tuner of the C ABI run on the ragged
+workload), applied with ``sdft_ragged_form_select``.
 
 At import of the package nothing is changed; ``ensure_applied()`` (called by
 ``Plan``) loads the file named by the environment variable SDFT_TUNE_CACHE, or
 else the table shipped with the package (``tuned_schedules.json``), once.
 
 CLI:  python -m paper_2504_07264_gb300.autotune [--out FILE] [--points P] [--reps R]
-                                               [--sizes N [N ...]]
+                                               [--sizes N [N ...]] [--ragged]
 """
 from __future__ import annotations
 
@@ -89,13 +94,44 @@ def tune(sizes=None, dtype: int = S.SDFT_F32, points: int = 1 << 26, reps: int =
     return {str(dtype): out}
 
 
+def tune_ragged(reps: int = 5, stream=None) -> dict:
+    """Run the work-queue plan tuner (``sdft_plan_ragged_autotune``) on the
+    ragged workload (10000 transforms, lengths 2^U{3..16}, seed 4) and select
+    the forms it keeps for later plans; returns {"ragged": {str(n): form}}
+    for every length 4 .. 65536 (lengths the workload lacks keep form 0)."""
+    import torch
+    root = os.path.dirname(HERE)
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import workloads
+    lengths, _, xr_h, xi_h = workloads.ragged_planes()
+    xr = torch.from_numpy(xr_h).cuda()
+    xi = torch.from_numpy(xi_h).cuda()
+    yr, yi = torch.empty_like(xr), torch.empty_like(xi)
+    with S.Plan(lengths=lengths) as plan:
+        plan.ragged_autotune(xr, xi, yr, yi, reps=reps, stream=stream)
+        forms = {}
+        for logn in range(2, 17):
+            n = 1 << logn
+            forms[str(n)] = plan.ragged_form(n) if (lengths == n).any() else 0
+    for n, f in forms.items():
+        S.lib().sdft_ragged_form_select(int(n), int(f))
+    return {"ragged": forms}
+
+
 def apply(table: dict, name: str | None = None) -> int:
-    """Select the recorded schedules of GPU ``name`` (default: the current
-    one); returns how many lengths were set."""
+    """Select the recorded schedules (and work-queue forms) of GPU ``name``
+    (default: the current one); returns how many lengths were set."""
     if name is None:
         name = gpu_name()
     applied = 0
     for dtype, per_n in table.get(name, {}).items():
+        if dtype == "ragged":
+            for n, form in per_n.items():
+                if 0 <= int(form) < max(0, S.sdft_ragged_form_count(int(n))) and \
+                        S.lib().sdft_ragged_form_select(int(n), int(form)) == S.SDFT_OK:
+                    applied += 1
+            continue
         for n, rec in per_n.items():
             idx = int(rec["index"])
             if idx < S.sdft_schedule_count(int(n), int(dtype)) and \
@@ -147,9 +183,18 @@ def main(argv=None) -> int:
     ap.add_argument("--sizes", type=int, nargs="+", default=None,
                     help="lengths to tune (default: every power of two 2 .. 65536); the "
                          "others keep their entries in --out")
+    ap.add_argument("--ragged", action="store_true",
+                    help="tune only the work-queue forms of ragged plans, on the ragged workload")
     a = ap.parse_args(argv)
     from . import build
     build.build()
+    if a.ragged:
+        ensure_applied()
+        table = tune_ragged()
+        save(table, a.out)
+        print("ragged forms:", table["ragged"])
+        print(f"wrote {a.out}")
+        return 0
     table = tune(sizes=a.sizes, points=a.points, reps=a.reps)
     save(table, a.out)
     for dtype, per_n in table.items():

@@ -153,7 +153,19 @@ const KernelInfo* cluster_kernel(int logn, int idx) {
     static const KernelInfo k15q = cluster_info<Cluster15q>(
         "N=32768: cluster of 8 CTAs of 128 threads, distributed shared memory, 256 x 128, "
         "radix [32,8]x[32,4]");
+    static const KernelInfo k16e = cluster_info<Cluster16e>(
+        "N=65536: cluster of 8 CTAs of 128 threads x 64 values, three per SM, distributed "
+        "shared memory, 256 x 256, radix [32,8]x[32,8]");
+    static const KernelInfo k15e = cluster_info<Cluster15e>(
+        "N=32768: cluster of 4 CTAs of 128 threads x 64 values, three per SM, distributed "
+        "shared memory, 256 x 128, radix [32,8]x[16,8]");
+    static const KernelInfo k14e = cluster_info<Cluster14e>(
+        "N=16384: cluster of 2 CTAs of 128 threads x 64 values, three per SM, distributed "
+        "shared memory, 128 x 128, radix [16,8]x[16,8]");
     if (logn == 15 && idx == 1) return &k15q;
+    if (logn == 16 && idx == 1) return &k16e;
+    if (logn == 15 && idx == 2) return &k15e;
+    if (logn == 14 && idx == 1) return &k14e;
     if (idx != 0) return nullptr;
     switch (logn) {
         case 14: return &k14;

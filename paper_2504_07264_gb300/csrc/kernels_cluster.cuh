@@ -71,12 +71,15 @@ __device__ __forceinline__ float ld_cluster(uint32_t addr) {
     return v;
 }
 
-template <int LOGA, int LOGC, int LOGQ, class SA, class SC, int THREADS_ = 256>
+template <int LOGA, int LOGC, int LOGQ, class SA, class SC, int THREADS_ = 256, int MINB_ = 0>
 struct ClusterCfg {
     using SA_ = SA;
     using SC_ = SC;
     static constexpr int THREADS = THREADS_;
-    static constexpr int MINB = 512 / THREADS;   // CTAs per SM: 64 K registers / (THREADS x 128)
+    // CTAs per SM: 64 K registers / (THREADS x 128) for 32 values per thread;
+    // the 64-value forms give the count explicitly (3 x 128 threads, <= 170
+    // registers each)
+    static constexpr int MINB = MINB_ > 0 ? MINB_ : 512 / THREADS;
     static constexpr int Q = 1 << LOGQ;
     static constexpr int A = 1 << LOGA, C = 1 << LOGC, N = A * C, LOGN = LOGA + LOGC;
     static constexpr int LOGCQ = LOGC - LOGQ, CQ = 1 << LOGCQ;   // pass-1 columns per CTA
@@ -175,13 +178,25 @@ __device__ __forceinline__ void pass1(LD ld, MID mid, float* const work, const i
     }
 }
 
+// The second barrier of pass 2 over the whole cluster: the arrive (release)
+// follows this CTA's remote reads, the wait precedes the first write that
+// reuses Y, and the step-0 register DFTs run in between.
+struct ClusterReadsDone {
+    __device__ __forceinline__ void after_gather() const { cluster_arrive(); }
+    __device__ __forceinline__ void before_scatter() const { cluster_wait(); }
+};
+
 // Pass 2: rows of Y from every CTA of the cluster, results to `st`.  Every
 // CTA's remote reads of this CTA's Y have finished when it returns.
 // `rank0`: the cluster rank of the first of the Q CTAs that hold the transform.
-template <class CFG, bool ADJ, class ST>
+// `rd`: the barrier that tells each CTA that the others' reads of its Y are
+// done (after_gather() right after the remote loads, before_scatter() before
+// Y is overwritten).
+template <class CFG, bool ADJ, class ST, class RD = ClusterReadsDone>
 __device__ __forceinline__ void pass2(ST st, float* const work, const uint32_t y_sh, const int tid,
                                       const int d, const uint32_t rank0,
-                                      const float2* __restrict__ tw, const W64& w) {
+                                      const float2* __restrict__ tw, const W64& w,
+                                      const RD rd = RD{}) {
     using SC = typename CFG::SC_;
     constexpr int A = CFG::A, C = CFG::C, CQ = CFG::CQ, AQ = CFG::AQ;
     const int sub2 = tid % AQ, tc = tid / AQ;
@@ -208,9 +223,9 @@ __device__ __forceinline__ void pass2(ST st, float* const work, const uint32_t y
     };
     float re[SC::E], im[SC::E];
     step_gather<SC, 0, ADJ>(re, im, tc, ld, xrd);
-    cluster_arrive();   // this CTA's remote reads are done
+    rd.after_gather();     // this CTA's remote reads are done
     step_compute<SC, 0, ADJ>(re, im, w);
-    cluster_wait();     // every CTA's reads of Y are done: Y may be overwritten
+    rd.before_scatter();   // every CTA's reads of Y are done: Y may be overwritten
     step_scatter<SC, 0, ADJ>(re, im, tc, twf, xw, st);
     __syncthreads();
     step_gather<SC, 1, ADJ>(re, im, tc, ld, xrd);
@@ -228,5 +243,18 @@ using Cluster16 = ClusterCfg<8, 8, 3, ClusterR256, ClusterR256>;   // 256 x 256,
 // 158 Gpts/s against 234 and 176 for the 256-thread forms: at N = 65536 only
 // 33 clusters of 16 fit and the pass-2 warps read 64-byte pieces.)
 using Cluster15q = ClusterCfg<8, 7, 3, ClusterR256, ClusterR128, 128>;
+// 64 values per thread: CTAs of 128 threads holding 8192 points, three per SM
+// (24 K points in flight per SM instead of 16 K), the same A x C splits and
+// Y layout as the 256-thread forms.
+using ClusterE256 = Steps<8, 6, 5, 3, 0>;   // 4 threads x 64 values, radix [32,8]
+using ClusterE128 = Steps<7, 6, 4, 3, 0>;   // 2 threads x 64 values, radix [16,8]
+using Cluster16e = ClusterCfg<8, 8, 3, ClusterE256, ClusterE256, 128, 3>;   // 256 x 256, Q = 8
+using Cluster15e = ClusterCfg<8, 7, 2, ClusterE256, ClusterE128, 128, 3>;   // 256 x 128, Q = 4
+using Cluster14e = ClusterCfg<7, 7, 1, ClusterE128, ClusterE128, 128, 3>;   // 128 x 128, Q = 2
+// 128-thread forms with 32 values per thread (4096 points per CTA), for the
+// work-queue kernel: N = 16384 on four CTAs, N = 8192 on two
+using ClusterR64 = Steps<6, 5, 3, 3, 0>;     // 2 threads x 32 values, radix [8,8]
+using Cluster14q = ClusterCfg<7, 7, 2, ClusterR128, ClusterR128, 128>;   // 128 x 128, Q = 4
+using Cluster13 = ClusterCfg<7, 6, 1, ClusterR128, ClusterR64, 128>;     // 128 x 64, Q = 2
 
 }  // namespace sdft

@@ -6,16 +6,23 @@
 
 namespace sdft {
 
-// The kernel runs as thread-block clusters of kRaggedCluster CTAs.  A cluster
-// claims one cluster item at a time:
-//   x = log2 N (2 .. 13): a group of up to 8 row items; CTA r of the cluster
-//       runs row item y + r if r < z
-//   x = kLong + log2 N (14 .. 16): long transforms y .. y + z - 1 of the long
-//       list, one per N / 8192 CTAs of the cluster (z <= 8 * 8192 / N)
-// A row item (x = log2 N, y = first transform in the row order, z = count)
-// is `per_item` transforms of one length run by one CTA.
-constexpr int kLong = 100;
+// The kernel runs as thread-block clusters of kRaggedCluster CTAs of 128
+// threads (three CTAs per SM).  Every length class runs one of its compiled
+// *forms* (a routine: radix split, values per thread, CTAs per transform,
+// transforms per tile).  A form holds a transform in the shared memory of
+// q = 8, 4 or 2 CTAs (a group of the cluster: ranks g*q .. g*q+q-1) or runs
+// a tile of transforms in one CTA (q = 1).  The work is split into four
+// phases by q; a cluster runs the q = 8 phase as one group, then splits into
+// two groups of four, then into pairs, then into single CTAs:
+//   phase 0..2 (q = 8, 4, 2): one item per transform, {routine, row start lo,
+//                             row start hi, N}, taken by the groups in turn
+//   phase 3    (q = 1)      : row items {routine, first transform in the row
+//                             order, count, 0}, claimed by each CTA
 constexpr int kRaggedCluster = 8;
+constexpr int kRaggedPhases = 4;
+constexpr int kRaggedRoutines = 48;      // routine codes 0 .. kRaggedRoutines - 1
+
+inline int ragged_phase_of(int q) { return q == 8 ? 0 : q == 4 ? 1 : q == 2 ? 2 : 3; }
 
 // Kernel arguments, passed by value.
 struct RaggedArgs {
@@ -23,37 +30,39 @@ struct RaggedArgs {
     const float* xi;
     float* yr;
     float* yi;
-    const long long* offsets;       // row items: row start (floats) of each transform, in work order
-    const int4* items;              // row items
-    const int4* citems;             // cluster items
-    int nitems;                     // cluster items
-    int* counter;                   // claimed cluster items (zero at launch)
-    const long long* long_offsets;  // long transforms: row start (floats)
-    int* never;                     // a word that stays zero (target of injected waits)
-    int* status;                    // plan status word (SDFT_ERR_TIMEOUT on a wait that gave up)
-    int wait_polls;                 // bound of every wait (polls of ~128 ns)
-    int inject;                     // tests: every long item first waits for `never` to become 1
-    unsigned alt;                   // bit l: class log2 N = l uses its alternative routine
-    const float2* tw[17];           // twiddle tables of each length class (by log2 N)
+    const int4* items[kRaggedPhases];   // each phase's items, in claim order
+    int nitems[kRaggedPhases];
+    const long long* offsets;           // row items: row start (floats) of each transform
+    int* counters;                      // [kRaggedPhases] claim counters (only the row phase
+                                        // claims), then a word that stays zero (all zeroed
+                                        // before each launch)
+    int* status;                        // plan status word (SDFT_ERR_TIMEOUT on a wait that gave up)
+    int wait_polls;                     // bound of every wait (polls)
+    int inject;                         // tests: every group item first waits for a word nothing sets
+    unsigned coupled;                   // bit p (p = 1, 2): the groups of phase p that share a
+                                        // cluster synchronise together (hardware cluster barrier)
+    const float2* tw[kRaggedRoutines];  // twiddle tables of each routine
     W64 w;
 };
 
-// One length class of the work-queue kernel.
-struct RaggedClass {
+// One compiled routine of the work-queue kernel.
+struct RaggedForm {
+    const char* name;
+    int code;                   // routine code (the item's first word)
     int logn;
-    int per_item;               // transforms per row item, or per cluster item (long classes)
-    bool large;                 // a long class: cluster items
+    int q;                      // CTAs per transform (8, 4, 2), or 1: a tile of one CTA
+    int per_item;               // q = 1: transforms per tile
     int ntables;
     TableDesc tables[4];
     int64_t tw_entries;
 };
 
-const RaggedClass* ragged_class(int logn);   // log2 N in [2, 16], else null
+int ragged_form_count(int logn);                 // log2 N in [2, 16], else 0
+const RaggedForm* ragged_form(int logn, int f);  // null past the last
 int ragged_threads();
 size_t ragged_smem();
 const void* ragged_kernel_fn(bool adj);
 cudaError_t ragged_prepare();
-int ragged_resident_ctas();                  // whole clusters resident over the GPU
-unsigned ragged_alt_classes();               // bit l: class l has an alternative routine
+int ragged_resident_ctas();                      // whole clusters resident over the GPU
 
 }  // namespace sdft

@@ -13,7 +13,6 @@
 #include <mutex>
 #include <new>
 #include <set>
-
 #include <vector>
 
 #include "../../include/sdft.h"
@@ -29,19 +28,20 @@ const KernelInfo* rows_candidate_1024(int logn, int idx);
 const KernelInfo* rows_candidate_big(int logn, int idx);
 const KernelInfo* rows_pf_candidate(int logn, int idx);
 
-// The work-queue schedule of a long length (cluster items of the ragged kernel).
+// The work-queue schedule of a long length: the persistent kernel of ragged
+// plans (ragged.cu) on a uniform batch, with the length's selected form.
 const KernelInfo* queue_candidate(int logn) {
     static KernelInfo q[17];
     static const bool init = [] {
         static const char* names[17] = {};
-        names[14] = "N=16384: work queue of cluster items, 4 transforms per cluster of 8 CTAs";
-        names[15] = "N=32768: work queue of cluster items, 2 transforms per cluster of 8 CTAs";
-        names[16] = "N=65536: work queue of cluster items, 1 transform per cluster of 8 CTAs";
+        names[14] = "N=16384: work queue of the persistent ragged kernel (clusters of 8 CTAs)";
+        names[15] = "N=32768: work queue of the persistent ragged kernel (clusters of 8 CTAs)";
+        names[16] = "N=65536: work queue of the persistent ragged kernel (clusters of 8 CTAs)";
         for (int l = 14; l <= 16; ++l) {
             q[l] = KernelInfo{};
             q[l].name = names[l];
             q[l].logn = l;
-            q[l].threads = 256;
+            q[l].threads = 128;
             q[l].transforms_per_cta = 1;
             q[l].launches = 1;
             q[l].queue = true;
@@ -78,7 +78,8 @@ const KernelInfo* f32_candidate(int logn, int idx) {
         while (rows_candidate_big(logn, n)) ++n;
         if (idx == n) return queue_candidate(14);
         if (idx == n + 1) return cluster_kernel(14, 0);
-        return idx == n + 2 ? rows_pf_candidate(14, 0) : nullptr;
+        if (idx == n + 2) return rows_pf_candidate(14, 0);
+        return idx == n + 3 ? cluster_kernel(14, 1) : nullptr;
     }
     if (logn >= 15 && logn <= 16) {
         if (idx == 0) return queue_candidate(logn);
@@ -122,24 +123,25 @@ struct HostStaging {
     float2* d_scratch = nullptr;       // second scratch set for the second slot
 };
 
-// State of a ragged plan: work order, work items and one CUDA graph per
-// direction (a memset of the work counter, then the persistent kernel).
+// State of a ragged plan: the form of every length class, the work items of
+// each phase and one CUDA graph per direction (a memset of the claim
+// counters, then the persistent kernel).
 struct RaggedState {
     bool on = false;
     bool uniform = false;             // a uniform batch of long transforms
     int64_t count = 0;
-    long long* d_offsets = nullptr;
-    int4* d_items = nullptr;           // row items
-    int4* d_citems = nullptr;          // cluster items
-    int nitems = 0;                    // cluster items
-    int nlong = 0;                     // long transforms
-    int* d_sync = nullptr;             // [work counter, a word that stays zero]
-    long long* d_long_offsets = nullptr;
-    int wait_polls = 1 << 23;          // ~1 s of 128 ns polls
-    int inject = 0;                    // tests: long items wait for a word nothing sets
-    unsigned alt = 0;                  // bit l: class l runs its alternative routine
-    const float2* tw[17] = {};
-    unsigned classes = 0;              // bit l set: some transform has log2 N = l
+    std::vector<signed char> logn;    // log2 N of every transform, caller's order
+    std::vector<long long> start;     // row start (floats) of every transform
+    int form[17] = {};                // form of every length class
+    unsigned classes = 0;             // bit l set: some transform has log2 N = l
+    const float2* rtw[kRaggedRoutines] = {};   // twiddle tables of every routine
+    int4* d_items[kRaggedPhases] = {};         // capacity `count` each
+    int nitems[kRaggedPhases] = {};
+    long long* d_offsets = nullptr;    // row items: row starts in work order
+    int* d_sync = nullptr;             // [claim counters of the phases, a word that stays zero]
+    int wait_polls = 1 << 23;          // bound of every device-side wait (polls)
+    int inject = 0;                    // tests: group items wait for a word nothing sets
+    unsigned coupled = 0x6u;           // bit p: phase p's groups of a cluster synchronise together
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     cudaGraphNode_t knode[2] = {nullptr, nullptr};
@@ -175,6 +177,8 @@ std::set<const sdft_plan*> g_registry;
 
 // process-wide schedule choice per log2 N for the FP32 path (autotuner)
 std::atomic<int> g_choice[17];
+// process-wide form of every length class for work-queue plans created later
+std::atomic<int> g_rform[17];
 
 int candidate_count(int logn, int dtype) {
     if (dtype != SDFT_F32) return split_kernel(logn, dtype) ? 1 : 0;
@@ -222,10 +226,9 @@ void free_plan_memory(sdft_plan* p) {
         if (r.graph[d]) cudaGraphDestroy(r.graph[d]);
     }
     if (r.d_offsets) cudaFree(r.d_offsets);
-    if (r.d_items) cudaFree(r.d_items);
-    if (r.d_citems) cudaFree(r.d_citems);
+    for (int ph = 0; ph < kRaggedPhases; ++ph)
+        if (r.d_items[ph]) cudaFree(r.d_items[ph]);
     if (r.d_sync) cudaFree(r.d_sync);
-    if (r.d_long_offsets) cudaFree(r.d_long_offsets);
 }
 
 bool ranges_overlap(const void* a, const void* b, size_t bytes) {
@@ -285,7 +288,7 @@ int launch(const sdft_plan* p, int direction, const float* xr, const float* xi, 
 }
 
 // Ragged plans: launch the direction's graph, building it on first use and
-// re-pointing its kernel node when the data pointers change.
+// re-pointing its kernel node when its arguments change.
 int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr,
                   float* yi, cudaStream_t stream) {
     RaggedState& r = p->rag;
@@ -295,18 +298,17 @@ int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi,
     a.xi = xi;
     a.yr = yr;
     a.yi = yi;
+    for (int ph = 0; ph < kRaggedPhases; ++ph) {
+        a.items[ph] = r.d_items[ph];
+        a.nitems[ph] = r.nitems[ph];
+    }
     a.offsets = r.d_offsets;
-    a.items = r.d_items;
-    a.citems = r.d_citems;
-    a.nitems = r.nitems;
-    a.counter = r.d_sync;
-    a.long_offsets = r.d_long_offsets;
-    a.never = r.d_sync + 1;
+    a.counters = r.d_sync;
     a.status = p->d_status;
     a.wait_polls = r.wait_polls;
     a.inject = r.inject;
-    a.alt = r.alt;
-    for (int l = 0; l < 17; ++l) a.tw[l] = r.tw[l];
+    a.coupled = r.coupled;
+    for (int c = 0; c < kRaggedRoutines; ++c) a.tw[c] = r.rtw[c];
     a.w = p->w64;
     void* kargs[] = {&a};
     cudaKernelNodeParams kp = {};
@@ -323,7 +325,7 @@ int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi,
         mp.dst = r.d_sync;
         mp.value = 0;
         mp.elementSize = sizeof(int);
-        mp.width = 2;
+        mp.width = kRaggedPhases + 1;
         mp.height = 1;
         mp.pitch = 0;
         cudaGraphNode_t mnode = nullptr;
@@ -367,80 +369,102 @@ int run(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr
     return launch(p, direction, xr, xi, yr, yi, stream, batch, scratch);
 }
 
-// Ragged plans, and uniform plans of long transforms: build the work queue
-// of the persistent cluster kernel (ragged.cu).  Long transforms (N >= 16384)
-// come first, longest first, grouped into cluster items of 8 * 8192 points
-// (one, two or four transforms); then the row items, longest first, grouped
-// eight to a cluster item.
-sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform) {
-    std::vector<int> logn((size_t)count);
-    int64_t total = 0;
-    for (int64_t t = 0; t < count; ++t) {
-        logn[(size_t)t] = log2_exact(lengths[t]);
-        total += lengths[t];
-        if (total > ((int64_t)1 << 40)) { fail(SDFT_ERR_INVALID_ARG); return nullptr; }
-    }
-    std::vector<long long> start((size_t)count);
-    {
-        long long o = 0;
-        for (int64_t t = 0; t < count; ++t) { start[(size_t)t] = o; o += lengths[t]; }
-    }
-    unsigned classes = 0;
-    std::vector<int4> citems;
-    // long transforms, longest first
-    std::vector<long long> long_off;
-    for (int l = kMaxLogN; l >= 2; --l) {
-        const RaggedClass* c = ragged_class(l);
-        if (!c->large) continue;
-        const int first = (int)long_off.size();
-        for (int64_t t = 0; t < count; ++t)
-            if (logn[(size_t)t] == l) long_off.push_back(start[(size_t)t]);
-        const int n_in = (int)long_off.size() - first;
-        if (n_in == 0) continue;
-        classes |= 1u << l;
-        for (int s0 = 0; s0 < n_in; s0 += c->per_item)
-            citems.push_back(make_int4(kLong + l, first + s0, std::min(c->per_item, n_in - s0), 0));
-    }
-    const int nlong = (int)long_off.size();
-    // row items, longest first, eight to a cluster item
+// Work items of a work-queue plan under its current forms (ragged.h): one
+// item per transform for the group phases (q = 8, 4, 2), longest first; row
+// tiles of `per_item` transforms for q = 1, longest first.  Uploads them on
+// `st` (the caller synchronises).
+int build_queue(sdft_plan* p, cudaStream_t st) {
+    RaggedState& r = p->rag;
+    std::vector<int4> items[kRaggedPhases];
     std::vector<long long> order_off;
-    std::vector<int4> items;
     for (int l = kMaxLogN; l >= 2; --l) {
-        const RaggedClass* c = ragged_class(l);
-        if (c->large) continue;
-        const int first = (int)order_off.size();
-        for (int64_t t = 0; t < count; ++t)
-            if (logn[(size_t)t] == l) order_off.push_back(start[(size_t)t]);
-        const int n_in = (int)order_off.size() - first;
-        if (n_in == 0) continue;
-        classes |= 1u << l;
-        for (int s0 = 0; s0 < n_in; s0 += c->per_item)
-            items.push_back(make_int4(l, first + s0, std::min(c->per_item, n_in - s0), 0));
+        if (!(r.classes & (1u << l))) continue;
+        const RaggedForm* f = ragged_form(l, r.form[l]);
+        if (!f) return SDFT_ERR_INVALID_ARG;
+        const int ph = ragged_phase_of(f->q);
+        if (f->q > 1) {
+            for (int64_t t = 0; t < r.count; ++t)
+                if (r.logn[(size_t)t] == l) {
+                    const long long o = r.start[(size_t)t];
+                    items[ph].push_back(make_int4(f->code, (int)(uint32_t)o,
+                                                  (int)(uint32_t)((unsigned long long)o >> 32),
+                                                  1 << l));
+                }
+        } else {
+            const int first = (int)order_off.size();
+            for (int64_t t = 0; t < r.count; ++t)
+                if (r.logn[(size_t)t] == l) order_off.push_back(r.start[(size_t)t]);
+            const int n_in = (int)order_off.size() - first;
+            for (int s0 = 0; s0 < n_in; s0 += f->per_item)
+                items[ph].push_back(make_int4(f->code, first + s0, std::min(f->per_item, n_in - s0), 0));
+        }
     }
-    for (int i0 = 0; i0 < (int)items.size(); i0 += kRaggedCluster)
-        citems.push_back(make_int4(items[(size_t)i0].x, i0,
-                                   std::min(kRaggedCluster, (int)items.size() - i0), 0));
+    for (int ph = 0; ph < kRaggedPhases; ++ph) {
+        if ((int64_t)items[ph].size() > r.count) return SDFT_ERR_INVALID_ARG;
+        if (!items[ph].empty() &&
+            cudaMemcpyAsync(r.d_items[ph], items[ph].data(), items[ph].size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return SDFT_ERR_CUDA;
+        r.nitems[ph] = (int)items[ph].size();
+    }
+    if (!order_off.empty() &&
+        cudaMemcpyAsync(r.d_offsets, order_off.data(), order_off.size() * sizeof(long long),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SDFT_ERR_CUDA;
+    return SDFT_OK;
+}
 
+// Rebuild a work-queue plan's items after a form change (synchronous; the
+// plan must have no work in flight that reads its items).
+int rebuild_queue(sdft_plan* p) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SDFT_ERR_CUDA;
+    int s = cudaDeviceSynchronize() == cudaSuccess ? SDFT_OK : SDFT_ERR_CUDA;
+    if (s == SDFT_OK) s = build_queue(p, st);
+    if (s == SDFT_OK && cudaStreamSynchronize(st) != cudaSuccess) s = SDFT_ERR_CUDA;
+    cudaStreamDestroy(st);
+    return s;
+}
+
+// Ragged plans, and uniform plans on the work-queue schedule: the persistent
+// kernel of ragged.cu.  Every length class starts with the process-wide form
+// selected for it; the twiddle tables of all forms of the plan's classes are
+// made at creation, so that a form change only rebuilds the work items.
+sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform) {
     sdft_plan* p = new (std::nothrow) sdft_plan();
     if (!p) { fail(SDFT_ERR_ALLOC); return nullptr; }
     p->magic = 0;
     p->dtype = SDFT_F32;
     p->n = uniform ? lengths[0] : 0;
     p->batch = count;
-    p->points = total;
     p->kern = nullptr;
     RaggedState& r = p->rag;
     r.on = true;
     r.uniform = uniform;
     r.count = count;
-    r.nitems = (int)citems.size();
-    r.nlong = nlong;
-    r.classes = classes;
+    int64_t total = 0;
+    try {
+        r.logn.resize((size_t)count);
+        r.start.resize((size_t)count);
+    } catch (...) {
+        delete p;
+        fail(SDFT_ERR_ALLOC);
+        return nullptr;
+    }
+    for (int64_t t = 0; t < count; ++t) {
+        const int l = log2_exact(lengths[t]);
+        r.logn[(size_t)t] = (signed char)l;
+        r.start[(size_t)t] = total;
+        total += lengths[t];
+        r.classes |= 1u << l;
+    }
+    p->points = total;
+    for (int l = 2; l <= kMaxLogN; ++l) {
+        const int f = g_rform[l].load();
+        r.form[l] = (f >= 0 && f < ragged_form_count(l)) ? f : 0;
+    }
     int status = SDFT_OK;
     cudaStream_t st = nullptr;
-    auto up = [&](void* dst, const void* src, size_t bytes) {
-        return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
-    };
     do {
         if (cudaGetDevice(&p->device) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
         int sms = 0;
@@ -454,36 +478,42 @@ sdft_plan* create_queue_plan(const int64_t* lengths, int64_t count, bool uniform
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             status = SDFT_ERR_CUDA; break;
         }
+        // twiddle tables of every form of every class present
         int64_t tw_total = 64;
-        int64_t base[17] = {};
-        for (int l = 2; l <= kMaxLogN; ++l)
-            if (classes & (1u << l)) { base[l] = tw_total; tw_total += ragged_class(l)->tw_entries; }
-        const size_t nl = (size_t)std::max(nlong, 1);
-        if (cudaMalloc(&p->d_tw, tw_total * sizeof(float2)) != cudaSuccess ||
-            cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&r.d_sync, 2 * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&r.d_offsets, std::max<size_t>(order_off.size(), 1) * sizeof(long long)) != cudaSuccess ||
-            cudaMalloc(&r.d_items, std::max<size_t>(items.size(), 1) * sizeof(int4)) != cudaSuccess ||
-            cudaMalloc(&r.d_citems, std::max<size_t>(citems.size(), 1) * sizeof(int4)) != cudaSuccess ||
-            cudaMalloc(&r.d_long_offsets, nl * sizeof(long long)) != cudaSuccess) {
-            status = SDFT_ERR_ALLOC; break;
+        int64_t base[kRaggedRoutines] = {};
+        for (int l = 2; l <= kMaxLogN; ++l) {
+            if (!(r.classes & (1u << l))) continue;
+            for (int f = 0; f < ragged_form_count(l); ++f) {
+                const RaggedForm* fm = ragged_form(l, f);
+                base[fm->code] = tw_total;
+                tw_total += std::max<int64_t>(fm->tw_entries, 1);
+            }
         }
+        const size_t cap = (size_t)std::max<int64_t>(count, 1);
+        bool ok = cudaMalloc(&p->d_tw, tw_total * sizeof(float2)) == cudaSuccess &&
+                  cudaMalloc(&p->d_status, sizeof(int)) == cudaSuccess &&
+                  cudaMalloc(&r.d_sync, (kRaggedPhases + 1) * sizeof(int)) == cudaSuccess &&
+                  cudaMalloc(&r.d_offsets, cap * sizeof(long long)) == cudaSuccess;
+        for (int ph = 0; ph < kRaggedPhases && ok; ++ph)
+            ok = cudaMalloc(&r.d_items[ph], cap * sizeof(int4)) == cudaSuccess;
+        if (!ok) { status = SDFT_ERR_ALLOC; break; }
         if (cudaMemsetAsync(p->d_status, 0, sizeof(int), st) != cudaSuccess ||
-            cudaMemsetAsync(r.d_sync, 0, 2 * sizeof(int), st) != cudaSuccess ||
-            !up(r.d_offsets, order_off.data(), order_off.size() * sizeof(long long)) ||
-            !up(r.d_items, items.data(), items.size() * sizeof(int4)) ||
-            !up(r.d_citems, citems.data(), citems.size() * sizeof(int4)) ||
-            !up(r.d_long_offsets, long_off.data(), long_off.size() * sizeof(long long))) {
+            cudaMemsetAsync(r.d_sync, 0, (kRaggedPhases + 1) * sizeof(int), st) != cudaSuccess) {
             status = SDFT_ERR_CUDA; break;
         }
         if (make_w64(&p->w64, p->d_tw, st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
         for (int l = 2; l <= kMaxLogN && status == SDFT_OK; ++l) {
-            if (!(classes & (1u << l))) continue;
-            const RaggedClass* c = ragged_class(l);
-            r.tw[l] = p->d_tw + base[l];
-            if (make_tables(p->d_tw + base[l], c->tables, c->ntables, st) != cudaSuccess)
-                status = SDFT_ERR_CUDA;
+            if (!(r.classes & (1u << l))) continue;
+            for (int f = 0; f < ragged_form_count(l) && status == SDFT_OK; ++f) {
+                const RaggedForm* fm = ragged_form(l, f);
+                r.rtw[fm->code] = p->d_tw + base[fm->code];
+                if (fm->ntables > 0 &&
+                    make_tables(p->d_tw + base[fm->code], fm->tables, fm->ntables, st) != cudaSuccess)
+                    status = SDFT_ERR_CUDA;
+            }
         }
+        if (status != SDFT_OK) break;
+        status = build_queue(p, st);
         if (status != SDFT_OK) break;
         if (cudaStreamSynchronize(st) != cudaSuccess) { status = SDFT_ERR_CUDA; break; }
     } while (0);
@@ -632,9 +662,12 @@ sdft_plan* sdft_plan_create_ragged(const int64_t* lengths, int64_t count, int dt
         fail(SDFT_ERR_UNSUPPORTED_DTYPE);
         return nullptr;
     }
+    int64_t total = 0;
     for (int64_t t = 0; t < count; ++t) {
         const int l = log2_exact(lengths[t]);
         if (l < 2 || l > kMaxLogN) { fail(SDFT_ERR_UNSUPPORTED_N); return nullptr; }
+        total += lengths[t];
+        if (total > ((int64_t)1 << 40)) { fail(SDFT_ERR_INVALID_ARG); return nullptr; }
     }
     if (dtype != SDFT_F32) { fail(SDFT_ERR_UNSUPPORTED_DTYPE); return nullptr; }
     return create_queue_plan(lengths, count, false);
@@ -794,7 +827,8 @@ int sdft_plan_set_wait_limit(sdft_plan* plan, int polls) {
 
 int sdft_plan_inject_unreachable_wait(sdft_plan* plan, int on) {
     if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
-    if (!plan->rag.on || plan->rag.nlong == 0) return fail(SDFT_ERR_INVALID_ARG);
+    if (!plan->rag.on || plan->rag.nitems[0] + plan->rag.nitems[1] + plan->rag.nitems[2] == 0)
+        return fail(SDFT_ERR_INVALID_ARG);
     plan->rag.inject = on ? 1 : 0;
     return SDFT_OK;
 }
@@ -833,27 +867,30 @@ int sdft_plan_launches(const sdft_plan* plan, int direction) {
 
 int sdft_plan_describe(const sdft_plan* plan, char* buf, int64_t len) {
     if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN), -1;
-    if (plan->rag.on && plan->rag.uniform) {
-        const KernelInfo* q = queue_candidate(log2_exact(plan->n));
-        return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
-                             "%s; one persistent launch (graph: counter memset + kernel), %d "
-                             "threads/CTA, %zu B smem, clusters of %d, grid %d, %d cluster items",
-                             q ? q->name : "work queue", ragged_threads(), ragged_smem(),
-                             kRaggedCluster, plan->grid, plan->rag.nitems);
-    }
     if (plan->rag.on) {
-        char cls[128] = {0};
+        const RaggedState& r = plan->rag;
+        char cls[512] = {0};
         int o = 0;
-        for (int l = 2; l <= kMaxLogN; ++l)
-            if (plan->rag.classes & (1u << l))
-                o += std::snprintf(cls + o, sizeof(cls) - (size_t)o, "%s%d", o ? "," : "", 1 << l);
+        for (int l = 2; l <= kMaxLogN && o < (int)sizeof(cls); ++l)
+            if (r.classes & (1u << l)) {
+                const RaggedForm* f = ragged_form(l, r.form[l]);
+                o += std::snprintf(cls + o, sizeof(cls) - (size_t)o, "%s%d: form %d (%s)",
+                                   o ? "; " : "", 1 << l, r.form[l],
+                                   f->q > 1 ? (f->q == 8 ? "8 CTAs" : f->q == 4 ? "4 CTAs" : "2 CTAs")
+                                            : "row tile");
+            }
+        const char* head = r.uniform ? (queue_candidate(log2_exact(plan->n))
+                                            ? queue_candidate(log2_exact(plan->n))->name
+                                            : "work queue")
+                                     : "ragged";
         return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
-                             "ragged: %lld transforms, %lld points, lengths {%s}; one persistent "
-                             "launch (graph: counter memset + kernel), %d threads/CTA, %zu B smem, "
-                             "clusters of %d, grid %d, %d cluster items",
-                             (long long)plan->rag.count, (long long)plan->points, cls,
+                             "%s: %lld transforms, %lld points, {%s}; one persistent launch "
+                             "(graph: counter memset + kernel), %d threads/CTA, %zu B smem, "
+                             "clusters of %d, grid %d, items per phase (8/4/2 CTAs, rows) "
+                             "%d/%d/%d/%d",
+                             head, (long long)r.count, (long long)plan->points, cls,
                              ragged_threads(), ragged_smem(), kRaggedCluster, plan->grid,
-                             plan->rag.nitems);
+                             r.nitems[0], r.nitems[1], r.nitems[2], r.nitems[3]);
     }
     return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0,
                          "%s; %d threads/CTA, %zu B smem, grid %d (occupancy %d), "
@@ -898,16 +935,73 @@ int sdft_schedule_selected(int64_t n, int dtype) {
     return dtype == SDFT_F32 ? g_choice[logn].load() : 0;
 }
 
-int sdft_plan_set_ragged_variants(sdft_plan* plan, unsigned mask) {
-    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
-    if (!plan->rag.on || (mask & ~ragged_alt_classes()) != 0) return fail(SDFT_ERR_INVALID_ARG);
-    plan->rag.alt = mask;
+int sdft_ragged_form_count(int64_t n) {
+    const int l = log2_exact(n);
+    const int c = (l >= 2 && l <= kMaxLogN) ? ragged_form_count(l) : 0;
+    return c > 0 ? c : -fail(SDFT_ERR_UNSUPPORTED_N);
+}
+
+int sdft_ragged_form_describe(int64_t n, int form, char* buf, int64_t len) {
+    const int l = log2_exact(n);
+    const RaggedForm* f = (l >= 2 && l <= kMaxLogN) ? ragged_form(l, form) : nullptr;
+    if (!f) return -fail(l >= 2 && l <= kMaxLogN ? SDFT_ERR_INVALID_ARG : SDFT_ERR_UNSUPPORTED_N);
+    return std::snprintf(buf, buf ? (size_t)std::max<int64_t>(len, 0) : 0, "%s", f->name);
+}
+
+int sdft_ragged_form_select(int64_t n, int form) {
+    const int l = log2_exact(n);
+    if (l < 2 || l > kMaxLogN) return fail(SDFT_ERR_UNSUPPORTED_N);
+    if (!ragged_form(l, form)) return fail(SDFT_ERR_INVALID_ARG);
+    g_rform[l].store(form);
     return SDFT_OK;
 }
 
-int sdft_plan_ragged_variants(const sdft_plan* plan) {
-    if (!plan_alive(plan) || !plan->rag.on) return -fail(SDFT_ERR_INVALID_ARG);
-    return (int)plan->rag.alt;
+int sdft_ragged_form_selected(int64_t n) {
+    const int l = log2_exact(n);
+    if (l < 2 || l > kMaxLogN) return -fail(SDFT_ERR_UNSUPPORTED_N);
+    return g_rform[l].load();
+}
+
+int sdft_plan_set_ragged_form(sdft_plan* plan, int64_t n, int form) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    const int l = log2_exact(n);
+    if (!plan->rag.on || l < 2 || l > kMaxLogN || !(plan->rag.classes & (1u << l)) ||
+        !ragged_form(l, form))
+        return fail(SDFT_ERR_INVALID_ARG);
+    int s = check_device(plan);
+    if (s != SDFT_OK) return fail(s);
+    RaggedState& r = plan->rag;
+    if (r.form[l] == form) return SDFT_OK;
+    const int prev = r.form[l];
+    r.form[l] = form;
+    s = rebuild_queue(plan);
+    if (s != SDFT_OK) {
+        r.form[l] = prev;
+        rebuild_queue(plan);
+        return fail(s);
+    }
+    return SDFT_OK;
+}
+
+int sdft_plan_set_ragged_coupling(sdft_plan* plan, unsigned mask) {
+    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
+    if (!plan->rag.on || (mask & ~0x6u) != 0) return fail(SDFT_ERR_INVALID_ARG);
+    plan->rag.coupled = mask;
+    return SDFT_OK;
+}
+
+int sdft_plan_ragged_coupling(const sdft_plan* plan) {
+    if (!plan_alive(plan)) return -fail(SDFT_ERR_BAD_PLAN);
+    if (!plan->rag.on) return -fail(SDFT_ERR_INVALID_ARG);
+    return (int)plan->rag.coupled;
+}
+
+int sdft_plan_ragged_form(const sdft_plan* plan, int64_t n) {
+    if (!plan_alive(plan)) return -fail(SDFT_ERR_BAD_PLAN);
+    const int l = log2_exact(n);
+    if (!plan->rag.on || l < 2 || l > kMaxLogN || !(plan->rag.classes & (1u << l)))
+        return -fail(SDFT_ERR_INVALID_ARG);
+    return plan->rag.form[l];
 }
 
 int sdft_plan_ragged_autotune(sdft_plan* plan, const float* xr, const float* xi, float* yr,
@@ -925,9 +1019,8 @@ int sdft_plan_ragged_autotune(sdft_plan* plan, const float* xr, const float* xi,
         return -fail(SDFT_ERR_CUDA);
     }
     RaggedState& r = plan->rag;
-    // milliseconds per forward call with variant mask `m` (one untimed call first)
-    auto time_mask = [&](unsigned m, float& ms) {
-        r.alt = m;
+    // milliseconds per forward call with the current forms (one untimed call first)
+    auto time_plan = [&](float& ms) {
         int q = run(plan, SDFT_FORWARD, xr, xi, yr, yi, st, plan->batch, nullptr);
         if (q == SDFT_OK && cudaEventRecord(e0, st) != cudaSuccess) q = SDFT_ERR_CUDA;
         for (int i = 0; i < reps && q == SDFT_OK; ++i)
@@ -939,23 +1032,33 @@ int sdft_plan_ragged_autotune(sdft_plan* plan, const float* xr, const float* xi,
         ms /= (float)reps;
         return q;
     };
-    // greedy, one length class at a time, longest first: keep the
-    // alternative routine only if it is faster by more than 1 %
-    unsigned mask = 0;
+    // greedy, one length class at a time, longest first: each form of the
+    // class in turn, keeping another form only if it is faster by more than 1 %
     float best = 0.f;
-    s = time_mask(mask, best);
-    const unsigned cand = ragged_alt_classes() & r.classes;
-    for (int l = kMaxLogN; l >= 0 && s == SDFT_OK; --l) {
-        if (!(cand & (1u << l))) continue;
-        float ms = 0.f;
-        s = time_mask(mask | (1u << l), ms);
-        if (s == SDFT_OK && ms < best * 0.99f) { mask |= 1u << l; best = ms; }
+    s = time_plan(best);
+    for (int l = kMaxLogN; l >= 2 && s == SDFT_OK; --l) {
+        if (!(r.classes & (1u << l)) || ragged_form_count(l) < 2) continue;
+        const int keep0 = r.form[l];
+        int keep = keep0;
+        for (int f = 0; f < ragged_form_count(l) && s == SDFT_OK; ++f) {
+            if (f == keep0) continue;
+            r.form[l] = f;
+            s = rebuild_queue(plan);
+            float ms = 0.f;
+            if (s == SDFT_OK) s = time_plan(ms);
+            if (s == SDFT_OK && ms < best * 0.99f) { keep = f; best = ms; }
+        }
+        r.form[l] = keep;
+        const int q = rebuild_queue(plan);
+        if (s == SDFT_OK) s = q;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    r.alt = mask;
     if (s != SDFT_OK) return -fail(s);
-    return (int)mask;
+    int mask = 0;
+    for (int l = 2; l <= kMaxLogN; ++l)
+        if ((r.classes & (1u << l)) && r.form[l] != 0) mask |= 1 << l;
+    return mask;
 }
 
 int sdft_autotune(int64_t n, int64_t batch, int dtype, const float* xr, const float* xi, float* yr,

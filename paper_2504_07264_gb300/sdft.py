@@ -55,8 +55,14 @@ _SIGS = {
     "sdft_plan_set_host_mode": ([_P, ctypes.c_int], ctypes.c_int),
     "sdft_plan_set_grid": ([_P, ctypes.c_int], ctypes.c_int),
     "sdft_plan_set_wait_limit": ([_P, ctypes.c_int], ctypes.c_int),
-    "sdft_plan_set_ragged_variants": ([_P, ctypes.c_uint], ctypes.c_int),
-    "sdft_plan_ragged_variants": ([_P], ctypes.c_int),
+    "sdft_ragged_form_count": ([_I64], ctypes.c_int),
+    "sdft_ragged_form_describe": ([_I64, ctypes.c_int, ctypes.c_char_p, _I64], ctypes.c_int),
+    "sdft_ragged_form_select": ([_I64, ctypes.c_int], ctypes.c_int),
+    "sdft_ragged_form_selected": ([_I64], ctypes.c_int),
+    "sdft_plan_set_ragged_form": ([_P, _I64, ctypes.c_int], ctypes.c_int),
+    "sdft_plan_ragged_form": ([_P, _I64], ctypes.c_int),
+    "sdft_plan_set_ragged_coupling": ([_P, ctypes.c_uint], ctypes.c_int),
+    "sdft_plan_ragged_coupling": ([_P], ctypes.c_int),
     "sdft_plan_ragged_autotune": ([_P, _P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "sdft_plan_inject_unreachable_wait": ([_P, ctypes.c_int], ctypes.c_int),
     "sdft_plan_grid": ([_P], ctypes.c_int),
@@ -192,12 +198,46 @@ def sdft_plan_set_wait_limit(plan, polls: int) -> int:
     return lib().sdft_plan_set_wait_limit(plan, polls)
 
 
-def sdft_plan_set_ragged_variants(plan, mask: int) -> int:
-    return lib().sdft_plan_set_ragged_variants(plan, mask)
+def sdft_ragged_form_count(n: int) -> int:
+    return lib().sdft_ragged_form_count(n)
 
 
-def sdft_plan_ragged_variants(plan) -> int:
-    return lib().sdft_plan_ragged_variants(plan)
+def sdft_ragged_form_describe(n: int, form: int) -> str:
+    need = lib().sdft_ragged_form_describe(n, form, None, 0)
+    if need < 0:
+        raise SdftError(-need, "sdft_ragged_form_describe")
+    buf = ctypes.create_string_buffer(need + 1)
+    lib().sdft_ragged_form_describe(n, form, buf, need + 1)
+    return buf.value.decode()
+
+
+def sdft_ragged_form_select(n: int, form: int) -> int:
+    """Select form `form` of length n for work-queue plans created later.  The
+    tuning table is applied first, so an explicit choice is never replaced by
+    it afterwards."""
+    from . import autotune
+    autotune.ensure_applied()
+    return lib().sdft_ragged_form_select(n, form)
+
+
+def sdft_ragged_form_selected(n: int) -> int:
+    return lib().sdft_ragged_form_selected(n)
+
+
+def sdft_plan_set_ragged_form(plan, n: int, form: int) -> int:
+    return lib().sdft_plan_set_ragged_form(plan, n, form)
+
+
+def sdft_plan_ragged_form(plan, n: int) -> int:
+    return lib().sdft_plan_ragged_form(plan, n)
+
+
+def sdft_plan_set_ragged_coupling(plan, mask: int) -> int:
+    return lib().sdft_plan_set_ragged_coupling(plan, mask)
+
+
+def sdft_plan_ragged_coupling(plan) -> int:
+    return lib().sdft_plan_ragged_coupling(plan)
 
 
 def sdft_plan_ragged_autotune(plan, xr, xi, yr, yi, reps: int, stream) -> int:
@@ -382,20 +422,32 @@ class Plan:
     def set_host_mode(self, mode: int) -> None:
         _check(sdft_plan_set_host_mode(self.handle, mode), "sdft_plan_set_host_mode")
 
-    @property
-    def ragged_variants(self) -> int:
-        """Ragged plans: bit l set = length 2^l runs its Eq. (6)-order routine."""
-        v = sdft_plan_ragged_variants(self.handle)
+    def ragged_form(self, n: int) -> int:
+        """Work-queue plans: the form length n runs in."""
+        v = sdft_plan_ragged_form(self.handle, n)
         if v < 0:
-            raise SdftError(-v, "sdft_plan_ragged_variants")
+            raise SdftError(-v, "sdft_plan_ragged_form")
         return v
 
-    def set_ragged_variants(self, mask: int) -> None:
-        _check(sdft_plan_set_ragged_variants(self.handle, mask), "sdft_plan_set_ragged_variants")
+    def set_ragged_form(self, n: int, form: int) -> None:
+        _check(sdft_plan_set_ragged_form(self.handle, n, form), "sdft_plan_set_ragged_form")
+
+    @property
+    def ragged_coupling(self) -> int:
+        """Work-queue plans: bit p set = the groups of phase p (p = 1: 4 CTAs,
+        p = 2: 2 CTAs) of a cluster share the hardware cluster barrier."""
+        v = sdft_plan_ragged_coupling(self.handle)
+        if v < 0:
+            raise SdftError(-v, "sdft_plan_ragged_coupling")
+        return v
+
+    def set_ragged_coupling(self, mask: int) -> None:
+        _check(sdft_plan_set_ragged_coupling(self.handle, mask), "sdft_plan_set_ragged_coupling")
 
     def ragged_autotune(self, xr, xi, yr, yi, reps: int = 10, stream=None) -> int:
-        """Time each length's routine forms on these device tensors (the
-        plan's layout) and keep the faster; returns the chosen mask."""
+        """Time each length's forms on these device tensors (the plan's
+        layout), one length at a time, longest first, and keep the fastest;
+        returns the mask of lengths (bit log2 N) left on a form other than 0."""
         v = sdft_plan_ragged_autotune(self.handle, xr.data_ptr(), xi.data_ptr(), yr.data_ptr(),
                                       yi.data_ptr(), reps, _stream_handle(stream))
         if v < 0:

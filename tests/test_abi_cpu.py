@@ -79,8 +79,8 @@ def test_bad_plan_handles(handle):
     assert S.sdft_execute(handle, 0, 16, 16, 16, 16, 0) == S.SDFT_ERR_BAD_PLAN
     assert S.sdft_execute_host(handle, 0, 16, 16, 16, 16, 0) == S.SDFT_ERR_BAD_PLAN
     assert S.sdft_plan_sync_status(handle, 0) == S.SDFT_ERR_BAD_PLAN
-    assert S.sdft_plan_set_ragged_variants(handle, 0) == S.SDFT_ERR_BAD_PLAN
-    assert S.sdft_plan_ragged_variants(handle) < 0
+    assert S.sdft_plan_set_ragged_form(handle, 1024, 0) == S.SDFT_ERR_BAD_PLAN
+    assert S.sdft_plan_ragged_form(handle, 1024) == -S.SDFT_ERR_BAD_PLAN
     assert S.sdft_plan_ragged_autotune(handle, 16, 16, 16, 16, 1, 0) == -S.SDFT_ERR_BAD_PLAN
     assert S.sdft_last_error() == S.SDFT_ERR_BAD_PLAN
     assert S.sdft_plan_n(handle) == 0 and S.sdft_plan_launches(handle, 0) == 0
@@ -94,3 +94,21 @@ def test_ragged_rejects_bad_lengths_before_cuda():
         h = S.sdft_plan_create_ragged(arr.ctypes.data if arr.size else 0, arr.size, S.SDFT_F32)
         assert h == 0
         assert S.sdft_last_error() in (S.SDFT_ERR_UNSUPPORTED_N, S.SDFT_ERR_INVALID_ARG)
+
+
+def test_ragged_forms_catalogue():
+    """Every length 4 .. 65536 has at least one work-queue form; form 0 is the
+    default; out-of-range lengths and forms are rejected on the host."""
+    for logn in range(2, 17):
+        n = 1 << logn
+        c = S.sdft_ragged_form_count(n)
+        assert c >= 1
+        for f in range(c):
+            assert S.sdft_ragged_form_describe(n, f).startswith(f"N={n}:")
+        assert S.lib().sdft_ragged_form_describe(n, c, None, 0) == -S.SDFT_ERR_INVALID_ARG
+    # the long lengths offer several CTA counts, the autotuner's choice
+    assert S.sdft_ragged_form_count(16384) >= 2 and S.sdft_ragged_form_count(32768) >= 2
+    for n in (2, 3, 131072):
+        assert S.sdft_ragged_form_count(n) == -S.SDFT_ERR_UNSUPPORTED_N
+    assert S.lib().sdft_ragged_form_select(1024, 99) == S.SDFT_ERR_INVALID_ARG
+    assert S.lib().sdft_ragged_form_select(2, 0) == S.SDFT_ERR_UNSUPPORTED_N

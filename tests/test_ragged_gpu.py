@@ -82,9 +82,9 @@ def test_every_class_and_many_items():
     assert _check_segments(lengths, off, xr, xi, yr, yi, 0, sorted(set(pick) | set(big))) <= TOL_F32
 
 
-# uniform-plan schedule with the same radix split as the ragged kernel's routine
-# (for N >= 16384 the cluster kernel)
-SAME_SCHEDULE = {16: 0, 1024: 0, 4096: 0, 16384: 3, 32768: 2, 65536: 2}
+# uniform-plan schedule with the same arithmetic as the ragged kernel's form 0
+# (the same radix split and tables; for N >= 16384 the 64-value cluster kernel)
+SAME_SCHEDULE = {16: 0, 1024: 0, 4096: 0, 16384: 5, 32768: 4, 65536: 3}
 
 
 def test_matches_uniform_plans_bitwise():
@@ -206,30 +206,88 @@ def test_full_ragged_workload_sampled():
     assert _check_segments(lengths, off, xr, xi, *hy, 0, sorted(pick)) <= TOL_F32
 
 
-def test_ragged_variants_and_autotune():
-    """Both routine forms of every row class match the oracle, the variant
-    mask is validated, and the plan's tuner leaves a valid mask in place."""
+def test_every_form_matches_oracle():
+    """Every compiled form of every length (row tiles of each radix split and
+    tile size, transforms held by 8, 4 or 2 CTAs) against the oracle, in both
+    directions, in one plan holding every length; the form switch rebuilds
+    the plan's work items between calls."""
+    from paper_2504_07264_gb300 import Plan
+    from paper_2504_07264_gb300 import sdft as S
+    lengths = np.array([1 << l for l in range(2, 17) for _ in range(3 + (l < 12) * 9)],
+                       dtype=np.int64)
+    lengths = np.random.default_rng(48).permutation(lengths)
+    xr, xi, off = _ragged_inputs(lengths, 48)
+    with Plan(lengths=lengths) as plan:
+        for logn in range(2, 17):
+            n = 1 << logn
+            assert plan.ragged_form(n) == 0
+            which = [t for t in range(len(lengths)) if lengths[t] == n]
+            for f in range(S.sdft_ragged_form_count(n)):
+                plan.set_ragged_form(n, f)
+                assert plan.ragged_form(n) == f
+                for direction in (0, 1):
+                    yr, yi = _run(plan, xr, xi, direction)
+                    err = _check_segments(lengths, off, xr, xi, yr, yi, direction, which)
+                    assert err <= TOL_F32, (n, f, direction, err)
+                assert plan.sync_status() == S.SDFT_OK
+            plan.set_ragged_form(n, 0)
+        with pytest.raises(S.SdftError):
+            plan.set_ragged_form(1024, S.sdft_ragged_form_count(1024))
+    with Plan(lengths=np.array([8, 1024], dtype=np.int64)) as plan:
+        with pytest.raises(S.SdftError):
+            plan.set_ragged_form(4096, 0)          # a length the plan does not hold
+    with Plan(1024, 4) as uplan:
+        with pytest.raises(S.SdftError):
+            uplan.set_ragged_form(1024, 0)
+
+
+def test_groups_of_every_size_in_one_launch():
+    """Forms that put transforms on groups of 8, 4 and 2 CTAs and on row tiles
+    in the same plan, with more transforms than groups in every phase, so that
+    groups split and finish at different times; the groups of 4 and of 2
+    synchronised with the whole cluster (coupled) or alone (mbarriers)."""
+    from paper_2504_07264_gb300 import Plan
+    from paper_2504_07264_gb300 import sdft as S
+    rng = np.random.default_rng(49)
+    lengths = np.concatenate([np.full(c, n, np.int64) for n, c in
+                              ((65536, 45), (32768, 70), (16384, 150), (8192, 200), (512, 900))])
+    lengths = rng.permutation(lengths)
+    xr, xi, off = _ragged_inputs(lengths, 49)
+    # N = 32768 on four CTAs (form 0) or eight (1); 16384 on two (0) or four
+    # (1); 8192 on two CTAs
+    cases = [(f15, f14, f13, c) for (f15, f14, f13) in ((0, 0, 0), (1, 1, 0), (0, 1, 0))
+             for c in (0x6, 0x0, 0x2, 0x4)]
+    for f15, f14, f13, coupling in cases:
+        with Plan(lengths=lengths) as plan:
+            assert plan.ragged_coupling == 0x6
+            plan.set_ragged_coupling(coupling)
+            assert plan.ragged_coupling == coupling
+            plan.set_ragged_form(32768, f15)
+            plan.set_ragged_form(16384, f14)
+            plan.set_ragged_form(8192, f13)
+            for direction in (0, 1):
+                yr, yi = _run(plan, xr, xi, direction)
+                assert plan.sync_status() == S.SDFT_OK
+                pick = sorted(set(rng.choice(len(lengths), 60, replace=False)) |
+                              {int(np.argmax(lengths == n)) for n in (65536, 32768, 16384, 8192)})
+                assert _check_segments(lengths, off, xr, xi, yr, yi, direction, pick) <= TOL_F32
+
+
+def test_ragged_autotune_keeps_valid_forms():
     import torch
 
     from paper_2504_07264_gb300 import Plan
     from paper_2504_07264_gb300 import sdft as S
-    lengths = np.array([1 << l for l in range(2, 17) for _ in range(3)], dtype=np.int64)
-    lengths = np.random.default_rng(48).permutation(lengths)
-    xr, xi, off = _ragged_inputs(lengths, 48)
+    lengths = np.array([1 << l for l in range(2, 17) for _ in range(4)], dtype=np.int64)
+    lengths = np.random.default_rng(50).permutation(lengths)
+    xr, xi, off = _ragged_inputs(lengths, 50)
     with Plan(lengths=lengths) as plan:
-        assert plan.ragged_variants == 0
-        plan.set_ragged_variants(0x3FE0)
-        assert plan.ragged_variants == 0x3FE0
-        for direction in (0, 1):
-            yr, yi = _run(plan, xr, xi, direction)
-            assert _check_segments(lengths, off, xr, xi, yr, yi, direction) <= TOL_F32
-        with pytest.raises(S.SdftError):
-            plan.set_ragged_variants(1 << 14)
         dxr, dxi = torch.from_numpy(xr).cuda(), torch.from_numpy(xi).cuda()
         m = plan.ragged_autotune(dxr, dxi, torch.empty_like(dxr), torch.empty_like(dxi), reps=2)
-        assert m >= 0 and (m & ~0x3FE0) == 0 and plan.ragged_variants == m
+        assert m >= 0
+        for logn in range(2, 17):
+            f = plan.ragged_form(1 << logn)
+            assert 0 <= f < S.sdft_ragged_form_count(1 << logn)
+            assert bool(m >> logn & 1) == (f != 0)
         yr, yi = _run(plan, xr, xi, 0)
         assert _check_segments(lengths, off, xr, xi, yr, yi, 0) <= TOL_F32
-    with Plan(1024, 4) as uplan:
-        with pytest.raises(S.SdftError):
-            uplan.set_ragged_variants(0)

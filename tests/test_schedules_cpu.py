@@ -64,5 +64,27 @@ def test_shipped_table_is_valid_if_present():
     for gpu, per_dtype in table.items():
         for dtype, per_n in per_dtype.items():
             for n, rec in per_n.items():
+                if dtype == "ragged":
+                    assert 0 <= rec < S.sdft_ragged_form_count(int(n)), (gpu, n)
+                    continue
                 assert 0 <= rec["index"] < S.sdft_schedule_count(int(n), int(dtype)), (gpu, n)
                 json.dumps(rec)
+
+
+def test_ragged_forms_save_apply(tmp_path):
+    """The work-queue forms are kept beside the schedules and applied as the
+    process-wide choice for later ragged plans."""
+    path = str(tmp_path / "tune.json")
+    A.save({"ragged": {"32768": 1, "16384": 1}}, path, name="Test GPU")
+    A.save({"0": {"4096": {"index": 0, "ms": [0.1], "schedules": ["a"]}}}, path, name="Test GPU")
+    table = A.load(path)
+    assert table["Test GPU"]["ragged"] == {"32768": 1, "16384": 1}
+    try:
+        assert A.apply(table, name="Test GPU") == 3
+        assert S.sdft_ragged_form_selected(32768) == 1
+        assert S.sdft_ragged_form_selected(16384) == 1
+    finally:
+        S.lib().sdft_ragged_form_select(32768, 0)
+        S.lib().sdft_ragged_form_select(16384, 0)
+    # an out-of-range form in a table is skipped, not applied
+    assert A.apply({"G": {"ragged": {"65536": 7}}}, name="G") == 0
