@@ -156,9 +156,8 @@ SDFT_API int sdft_plan_set_grid(sdft_plan* plan, int grid);
 SDFT_API int sdft_plan_grid(const sdft_plan* plan);
 
 /* Bound of the device-side waits of a work-queue plan (ragged plans, and
- * uniform plans on a work-queue schedule): the barriers of the groups of 4
- * and 2 CTAs that share a transform, and the wait added by the testing hook
- * below.  Every such wait polls at most `polls` times (default 2^23); past
+ * uniform plans on a work-queue schedule).  Their kernel needs no waits to
+ * compute; the only one is the wait added by the testing hook below.  Every such wait polls at most `polls` times (default 2^23); past
  * that the kernel records SDFT_ERR_TIMEOUT in the status word, stops waiting
  * anywhere and carries on (the results of that call are then undefined).  The status stays set, and later
  * calls skip their waits too, until sdft_plan_sync_status reads and clears it.
@@ -194,14 +193,6 @@ SDFT_API int sdft_ragged_form_selected(int64_t n);
 SDFT_API int sdft_plan_set_ragged_form(sdft_plan* plan, int64_t n, int form);
 /* The form length n runs in on this plan (>= 0), or -status. */
 SDFT_API int sdft_plan_ragged_form(const sdft_plan* plan, int64_t n);
-/* How the groups of 4 and of 2 CTAs (phases 1 and 2) synchronise: with bit p
- * of `mask` set, the 8 / q transforms that the groups of one cluster run at a
- * time share the hardware cluster barrier (a group without a transform waits
- * with the others); with it clear, every group synchronises alone through
- * mbarriers that its CTAs arrive on remotely.  Default 0x6 (both coupled).
- * SDFT_ERR_INVALID_ARG for other plans or bits outside 0x6. */
-SDFT_API int sdft_plan_set_ragged_coupling(sdft_plan* plan, unsigned mask);
-SDFT_API int sdft_plan_ragged_coupling(const sdft_plan* plan);
 /* Autotune a work-queue plan on the caller's device buffers (the plan's
  * layout, read xr/xi, written yr/yi): one length at a time, longest first,
  * time the plan's forward call with each form of that length (`reps` timed

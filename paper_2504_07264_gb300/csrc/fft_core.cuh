@@ -286,4 +286,10 @@ __device__ __forceinline__ void run_steps(const int t, const W64& w, LD ld, XW x
 // stride-32 and stride-16 column writes free of bank conflicts.
 __device__ __forceinline__ int pad32(int L) { return L + (L >> 5); }
 
+// The same without padding: element L at L ^ ((L >> 5) & 31), i.e. each line
+// of 32 words rotated by XOR with its line index.  A stride-32 column write
+// (one element per lane, lanes 32 apart) then falls on 32 banks, as do reads
+// of 32 consecutive elements; the exchange takes exactly N words per plane.
+__device__ __forceinline__ int swz32(int L) { return L ^ ((L >> 5) & 31); }
+
 }  // namespace sdft

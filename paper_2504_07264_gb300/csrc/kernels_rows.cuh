@@ -21,13 +21,17 @@
 namespace sdft {
 
 template <int LOGN, int LOGE, int LR0, int LR1, int LR2, int G_, int SBX_ = 0, int MINB_ = 1,
-          bool DIT = false>
+          bool DIT = false, bool SWZ_ = false>
 struct RowCfg {
     using S = Steps<LOGN, LOGE, LR0, LR1, LR2, DIT>;
     static constexpr int G = G_;
     static constexpr int THREADS = S::T * G;
     static constexpr int MINB = MINB_;
-    static constexpr int PLANE = S::N + (S::N >> 5);
+    // SWZ: the exchange is XOR-swizzled (swz32) rather than padded (pad32),
+    // so it takes exactly N words per plane (conflict-free for the splits it
+    // is used with: every step's columns 32 lanes apart or consecutive)
+    static constexpr bool SWZ = SWZ_;
+    static constexpr int PLANE = S::N + (SWZ ? 0 : (S::N >> 5));
     static constexpr int BUF = 2 * PLANE + SBX_;
     static constexpr size_t SMEM = S::NS > 1 ? (size_t)G * BUF * sizeof(float) : 0;
     // Step-0 rotations W_N^{nl d} (d < R0, nl < Q0 = N / R0).  For Q0 >= 64
@@ -101,12 +105,12 @@ __device__ __forceinline__ void rows_tile(const float* gxr, const float* gxi, fl
         else __syncthreads();
     };
     auto xw = [&](int L, float r, float i) {
-        const int p = pad32(L);
+        const int p = CFG::SWZ ? swz32(L) : pad32(L);
         s_re[p] = r;
         s_im[p] = i;
     };
     auto xrd = [&](int L, float& r, float& i) {
-        const int p = pad32(L);
+        const int p = CFG::SWZ ? swz32(L) : pad32(L);
         r = s_re[p];
         i = s_im[p];
     };
@@ -335,12 +339,12 @@ k_rows_pf(const float* xr, const float* xi, float* yr, float* yi, long long batc
     if (tid == 0 && blockIdx.x < ntiles) { load(blockIdx.x); pending = true; }
     uint32_t ph = 0;
     auto xw = [&](int L, float r, float i) {
-        const int p = pad32(L);
+        const int p = RC::SWZ ? swz32(L) : pad32(L);
         s_re[p] = r;
         s_im[p] = i;
     };
     auto xrd = [&](int L, float& r, float& i) {
-        const int p = pad32(L);
+        const int p = RC::SWZ ? swz32(L) : pad32(L);
         r = s_re[p];
         i = s_im[p];
     };

@@ -58,19 +58,13 @@ const FormTable& forms() {
         add(row_form<R3>("N=8: tile of 128 transforms, 1 thread each", kR3));
         add(row_form<R4>("N=16: tile of 128 transforms, 1 thread each", kR4));
         add(row_form<R5>("N=32: tile of 128 transforms, 1 thread each, radix [32]", kR5));
-        add(row_form<R5D>("N=32: tile of 128 transforms, radix [32], Eq. (6) order", kR5D));
         add(row_form<R6>("N=64: tile of 16 transforms, 8 threads each, radix [8,8]", kR6));
-        add(row_form<R6D>("N=64: tile of 16 transforms, radix [8,8], Eq. (6) order", kR6D));
         add(row_form<R7>("N=128: tile of 16 transforms, 8 threads each, radix [16,8]", kR7));
-        add(row_form<R7D>("N=128: tile of 16 transforms, radix [16,8], Eq. (6) order", kR7D));
         add(row_form<R8>("N=256: tile of 8 transforms, 16 threads each, radix [16,16]", kR8));
-        add(row_form<R8D>("N=256: tile of 8 transforms, radix [16,16], Eq. (6) order", kR8D));
         add(row_form<R8b>("N=256: tile of 16 transforms, 8 threads x 32 values, radix [32,8]", kR8b));
         add(row_form<R9>("N=512: tile of 8 transforms, 16 threads each, radix [32,16]", kR9));
-        add(row_form<R9D>("N=512: tile of 8 transforms, radix [32,16], Eq. (6) order", kR9D));
         add(row_form<R9b>("N=512: tile of 4 transforms, 32 threads each, radix [16,16,2]", kR9b));
         add(row_form<R10>("N=1024: tile of 4 transforms, 32 threads each, radix [32,32]", kR10));
-        add(row_form<R10D>("N=1024: tile of 4 transforms, radix [32,32], Eq. (6) order", kR10D));
         add(row_form<R11>("N=2048: tile of 2 transforms, 64 threads each, radix [32,16,4]", kR11));
         add(row_form<R12>("N=4096: tile of 1 transform, 128 threads, radix [32,32,4]", kR12));
         add(group_form<Cluster13>("N=8192: 2 CTAs per transform, distributed shared memory, 128 x 64", kC13));

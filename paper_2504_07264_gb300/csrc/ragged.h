@@ -15,7 +15,8 @@ namespace sdft {
 // phases by q; a cluster runs the q = 8 phase as one group, then splits into
 // two groups of four, then into pairs, then into single CTAs:
 //   phase 0..2 (q = 8, 4, 2): one item per transform, {routine, row start lo,
-//                             row start hi, N}, taken by the groups in turn
+//                             row start hi, N}, taken by the groups in turn; the
+//                             groups of a cluster share its barriers
 //   phase 3    (q = 1)      : row items {routine, first transform in the row
 //                             order, count, 0}, claimed by each CTA
 constexpr int kRaggedCluster = 8;
@@ -39,8 +40,6 @@ struct RaggedArgs {
     int* status;                        // plan status word (SDFT_ERR_TIMEOUT on a wait that gave up)
     int wait_polls;                     // bound of every wait (polls)
     int inject;                         // tests: every group item first waits for a word nothing sets
-    unsigned coupled;                   // bit p (p = 1, 2): the groups of phase p that share a
-                                        // cluster synchronise together (hardware cluster barrier)
     const float2* tw[kRaggedRoutines];  // twiddle tables of each routine
     W64 w;
 };

@@ -15,28 +15,25 @@
 //            memory,
 //   phase 3: row tiles of one CTA (transforms of up to 8192 points).
 // A cluster runs phase 0 as one group, then splits into two groups of four,
-// then into four pairs, then into single CTAs; groups never merge again and
-// synchronise only their own CTAs: the whole cluster with the hardware cluster
-// barrier, smaller groups with mbarriers that each CTA of the group arrives on
-// remotely (one thread per CTA, release at cluster scope; the polling thread
-// acquires, then releases its CTA with a CTA barrier).  Transforms that share
-// a cluster do not wait for each other.
-//
-// Work: in a group phase the grid's groups take the phase's transforms in turn
-// (group g: items g, g + G, ...), which needs no claims because the items of a
-// class cost the same, and lets every CTA bring its share of the group's next
-// transform into L2 a whole item ahead.  Row tiles, of very different sizes,
-// are claimed one at a time by each CTA with an atomicAdd (the next claim is
-// made while the current tile runs); early groups thereby take more of them.
+// then into four pairs, then into single CTAs.  In a group phase the grid's
+// groups take the phase's transforms in turn (group g: items g, g + G, ...),
+// which needs no claims because the items of a class cost the same, and lets
+// every CTA bring its share of the group's next transform into L2 a whole item
+// ahead; the PER = 8 / q transforms a cluster holds at a time share the
+// hardware cluster barrier (a group without a transform in the last round
+// takes the barriers only).  Row tiles, of very different sizes, are claimed
+// one at a time by each CTA with an atomicAdd (the next claim is made while
+// the current tile runs), so CTAs that finish their groups early take more of
+// them.  (Groups synchronising alone through mbarriers measured no faster and
+// doubled the kernel's code, which the instruction cache pays for.)
 //
 // A transform is computed with the same arithmetic and tables as the uniform
 // kernel of the same form.  The row-tile claim counter is zeroed by a memset
 // node that precedes the kernel in the plan's CUDA graph.  Every wait is bounded:
 // past its limit it records SDFT_ERR_TIMEOUT in the plan's status word, and
-// once the word is set no wait blocks any more (the results of that launch are
-// undefined, but every access stays within the plan's buffers and every CTA
-// keeps its shared memory until its cluster ends).  For tests, a plan can make
-// every group item first wait for a word that nothing sets.
+// once the word is set no wait blocks any more.  The only such wait is the
+// testing hook: a plan can make every group item first wait for a word that
+// nothing sets.
 #pragma once
 
 #include "../../include/sdft.h"
@@ -56,26 +53,19 @@ using R2 = RowCfg<2, 2, 2, 0, 0, 128>;
 using R3 = RowCfg<3, 3, 3, 0, 0, 128>;
 using R4 = RowCfg<4, 4, 4, 0, 0, 128>;
 using R5 = RowCfg<5, 5, 5, 0, 0, 128>;
-using R5D = RowCfg<5, 5, 5, 0, 0, 128, 0, 1, true>;
 using R6 = RowCfg<6, 3, 3, 3, 0, 16, 2>;
-using R6D = RowCfg<6, 3, 3, 3, 0, 16, 2, 1, true>;
 using R7 = RowCfg<7, 4, 4, 3, 0, 16>;
-using R7D = RowCfg<7, 4, 4, 3, 0, 16, 0, 1, true>;
 using R8 = RowCfg<8, 4, 4, 4, 0, 8>;
-using R8D = RowCfg<8, 4, 4, 4, 0, 8, 0, 1, true>;
 using R8b = RowCfg<8, 5, 5, 3, 0, 16, 8>;           // 8 threads x 32 values, radix [32,8]
 using R9 = RowCfg<9, 5, 5, 4, 0, 8, 16>;
-using R9D = RowCfg<9, 5, 5, 4, 0, 8, 16, 1, true>;
 using R9b = RowCfg<9, 4, 4, 4, 1, 4>;               // 32 threads, radix [16,16,2]
 using R10 = RowCfg<10, 5, 5, 5, 0, 4>;
-using R10D = RowCfg<10, 5, 5, 5, 0, 4, 0, 1, true>;
 using R11 = RowCfg<11, 5, 5, 4, 2, 2>;              // 64 threads, radix [32,16,4]
 using R12 = RowCfg<12, 5, 5, 5, 2, 1>;              // 128 threads, radix [32,32,4]
 
 // routine codes (the first word of every work item)
 enum : int {
-    kR2, kR3, kR4, kR5, kR5D, kR6, kR6D, kR7, kR7D, kR8, kR8D, kR8b, kR9, kR9D, kR9b,
-    kR10, kR10D, kR11, kR12,
+    kR2, kR3, kR4, kR5, kR6, kR7, kR8, kR8b, kR9, kR9b, kR10, kR11, kR12,
     kC13, kC14e, kC14q, kC15e, kC15q, kC16e, kRoutineCount
 };
 static_assert(kRoutineCount <= kRaggedRoutines, "routine table");
@@ -91,15 +81,15 @@ constexpr size_t smax(size_t a, size_t b) { return a > b ? a : b; }
 struct RaggedTail {
     int4 work[2];          // row tiles: this CTA's claimed records
     int4 next[2];          // group phases: the group's next item, alternating slots
-    uint64_t bar[2][2];    // mbarriers of the groups of 4 and of 2: [A, B]
     int ok;                // outcome of a bounded wait, for the whole CTA
 };
 // Every routine fits in 64 KiB: three CTAs of 64 KiB (plus the 1 KiB the
 // runtime reserves per CTA and the 128-byte tail) stay within the 196 KiB
 // shared-memory carveout, which leaves 60 KiB of L1 for the rotation tables
 // and the input lines; 2 KiB more per CTA forces the 228 KiB carveout, halves
-// L1 and cost 15 % at N = 65536 (a transform of 8192 points therefore runs on
-// two CTAs rather than as a row tile).
+// L1 and cost 15 % at N = 65536.  (A transform of 8192 points runs on two
+// CTAs: a one-CTA tile of it, 128 threads x 64 values with an XOR-swizzled
+// exchange of exactly 64 KiB, measured 145 against 152 Gpts/s.)
 constexpr size_t kData = smax(
     smax(smax(R9::SMEM, R10::SMEM), smax(R11::SMEM, R12::SMEM)),
     smax(smax(smax(Cluster13::SMEM, Cluster14e::SMEM), smax(Cluster14q::SMEM, Cluster15e::SMEM)),
@@ -117,14 +107,6 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-// the status word, read without ordering anything (an acquire at GPU scope
-// would also discard this SM's L1 lines, the rotation tables among them)
-__device__ __forceinline__ int ld_status(const int* p) {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // Thread 0 waits (bounded) until *word >= target; the CTA learns the outcome.
 // false: the wait gave up now or an earlier one did (status already set).
 __device__ __forceinline__ bool cta_wait(const int* word, int target, const RaggedArgs& a,
@@ -146,65 +128,6 @@ __device__ __forceinline__ bool cta_wait(const int* word, int target, const Ragg
     __syncthreads();
     return ok;
 }
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(addr), "r"(count) : "memory");
-}
-// One arrival on the mbarrier at `cluster_addr` (any CTA of the cluster),
-// ordering this thread's earlier memory operations before it (release,
-// cluster scope).
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];"
-                 :: "r"(cluster_addr) : "memory");
-}
-// true once the phase of parity `parity` of this CTA's mbarrier has completed
-// (acquire, cluster scope); never suspends the thread (the arrivals come from
-// other CTAs, and a polling test reacts to them at once)
-__device__ __forceinline__ bool mbar_test_wait(uint32_t addr, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
-    return ok != 0;
-}
-
-// Barrier of the Q < 8 CTAs g0 .. g0 + Q - 1 of the cluster on the mbarrier
-// `bar` (the same shared-memory offset in each of them, Q arrivals per
-// phase).  Every thread of the CTA calls it.  The CTA barrier first orders the
-// CTA's shared-memory accesses before thread 0's release arrivals; thread 0
-// then waits (bounded) for the phase and the second CTA barrier passes its
-// acquire on to every thread.
-template <int Q>
-__device__ __forceinline__ void group_sync(const uint32_t bar, const uint32_t g0,
-                                           uint32_t& parity, const RaggedArgs& a) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int m = 0; m < Q; ++m) mbar_arrive_cluster(map_rank(bar, g0 + (uint32_t)m));
-        bool ok = mbar_test_wait(bar, parity);
-        for (int i = 0; i < a.wait_polls && !ok; ++i) {
-            // after a timeout anywhere nothing waits any more
-            if ((i & 1023) == 1023 && ld_status(a.status) != 0) break;
-            ok = mbar_test_wait(bar, parity);
-        }
-        if (!ok && ld_status(a.status) == 0) atomicCAS(a.status, 0, SDFT_ERR_TIMEOUT);
-    }
-    parity ^= 1u;
-    __syncthreads();
-}
-
-// pass 2's reads-done barrier for a group of Q < 8 CTAs: the arrivals are made
-// once the remote values are in registers and used (after the step-0 register
-// DFTs), then the wait, before Y is overwritten.
-template <int Q>
-struct GroupReadsDone {
-    uint32_t bar, g0;
-    uint32_t* parity;
-    const RaggedArgs* a;
-    __device__ __forceinline__ void after_gather() const {}
-    __device__ __forceinline__ void before_scatter() const { group_sync<Q>(bar, g0, *parity, *a); }
-};
 
 // the record that ends a phase
 __device__ __forceinline__ int4 end_record() { return make_int4(-1, 0, 0, 0); }
@@ -252,23 +175,17 @@ __device__ __forceinline__ void group_item(const RaggedArgs& a, const int4 rec, 
 // within a class, so no claims are needed; at the top of each item every CTA
 // brings its share of the group's next transform into L2.
 template <int Q, int PHASE, bool ADJ>
-__device__ __forceinline__ void group_phase(const RaggedArgs& a, float* smem, const uint32_t rank,
-                                            const uint32_t bar_a, const uint32_t bar_b) {
+__device__ __forceinline__ void group_phase(const RaggedArgs& a, float* smem, const uint32_t rank) {
     static_assert(Q == (kRaggedCluster >> PHASE), "a phase's groups hold its routines' transforms");
     constexpr int PER = kRaggedCluster / Q;   // groups per cluster
     const uint32_t g0 = rank & ~(uint32_t)(Q - 1), q = rank & (uint32_t)(Q - 1);
     const int sub = (int)(rank / Q);
     const int stride = (int)(gridDim.x / kRaggedCluster) * PER;   // groups in the grid
-    // coupled: the PER transforms a cluster runs at once share the hardware
-    // cluster barrier (a group without a transform takes the barriers only);
-    // otherwise every group synchronises alone with its mbarriers
-    const bool coupled = Q == kRaggedCluster || ((a.coupled >> PHASE) & 1u);
-    uint32_t pa = 0, pb = 0;
-    auto sync_cluster = [] {
+    auto sync = [] {
         cluster_arrive();
         cluster_wait();
     };
-    auto sync_group = [&] { group_sync<Q>(bar_a, g0, pa, a); };
+    const ClusterReadsDone rd{};
     // Thread 0 issues the load of the group's next item at the top of the
     // current one and, between the two register steps of pass 1 (once it has
     // arrived), stores it into a slot of the CTA's tail and starts the L2
@@ -280,7 +197,7 @@ __device__ __forceinline__ void group_phase(const RaggedArgs& a, float* smem, co
     int base = (int)cluster_id() * PER;   // the cluster's first item of this round
     int par = 0;
     int4 rec = load_item(a, PHASE, base + sub);
-    while (coupled ? base < a.nitems[PHASE] : rec.x >= 0) {
+    while (base < a.nitems[PHASE]) {      // the same number of rounds for every CTA of a cluster
         base += stride;
         int4 nxt = end_record();
         if (threadIdx.x == 0) nxt = load_item(a, PHASE, base + sub);
@@ -296,30 +213,18 @@ __device__ __forceinline__ void group_phase(const RaggedArgs& a, float* smem, co
                 }
             }
         };
-        if (coupled) {
-            const ClusterReadsDone rd{};
-            switch (rec.x) {
-                case kC16e: if constexpr (Q == 8) group_item<Cluster16e, ADJ>(a, rec, smem, q, g0, mid, sync_cluster, rd); break;
-                case kC15q: if constexpr (Q == 8) group_item<Cluster15q, ADJ>(a, rec, smem, q, g0, mid, sync_cluster, rd); break;
-                case kC15e: if constexpr (Q == 4) group_item<Cluster15e, ADJ>(a, rec, smem, q, g0, mid, sync_cluster, rd); break;
-                case kC14q: if constexpr (Q == 4) group_item<Cluster14q, ADJ>(a, rec, smem, q, g0, mid, sync_cluster, rd); break;
-                case kC14e: if constexpr (Q == 2) group_item<Cluster14e, ADJ>(a, rec, smem, q, g0, mid, sync_cluster, rd); break;
-                case kC13: if constexpr (Q == 2) group_item<Cluster13, ADJ>(a, rec, smem, q, g0, mid, sync_cluster, rd); break;
-                default:   // no transform for this group in this round
-                    if (threadIdx.x == 0) tl->next[par] = nxt;
-                    sync_cluster();
-                    sync_cluster();
-                    break;
-            }
-        } else if constexpr (Q < kRaggedCluster) {
-            const GroupReadsDone<Q> rd{bar_b, g0, &pb, &a};
-            switch (rec.x) {
-                case kC15e: if constexpr (Q == 4) group_item<Cluster15e, ADJ>(a, rec, smem, q, g0, mid, sync_group, rd); break;
-                case kC14q: if constexpr (Q == 4) group_item<Cluster14q, ADJ>(a, rec, smem, q, g0, mid, sync_group, rd); break;
-                case kC14e: if constexpr (Q == 2) group_item<Cluster14e, ADJ>(a, rec, smem, q, g0, mid, sync_group, rd); break;
-                case kC13: if constexpr (Q == 2) group_item<Cluster13, ADJ>(a, rec, smem, q, g0, mid, sync_group, rd); break;
-                default: break;
-            }
+        switch (rec.x) {
+            case kC16e: if constexpr (Q == 8) group_item<Cluster16e, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
+            case kC15q: if constexpr (Q == 8) group_item<Cluster15q, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
+            case kC15e: if constexpr (Q == 4) group_item<Cluster15e, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
+            case kC14q: if constexpr (Q == 4) group_item<Cluster14q, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
+            case kC14e: if constexpr (Q == 2) group_item<Cluster14e, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
+            case kC13: if constexpr (Q == 2) group_item<Cluster13, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
+            default:   // no transform for this group in this round: the barriers only
+                if (threadIdx.x == 0) tl->next[par] = nxt;
+                sync();
+                sync();
+                break;
         }
         rec = tl->next[par];
         par ^= 1;
@@ -357,19 +262,13 @@ __device__ __forceinline__ void row_phase(const RaggedArgs& a, float* smem, int4
             case kR3: row_tile<R3, ADJ>(a, rec, smem); break;
             case kR4: row_tile<R4, ADJ>(a, rec, smem); break;
             case kR5: row_tile<R5, ADJ>(a, rec, smem); break;
-            case kR5D: row_tile<R5D, ADJ>(a, rec, smem); break;
             case kR6: row_tile<R6, ADJ>(a, rec, smem); break;
-            case kR6D: row_tile<R6D, ADJ>(a, rec, smem); break;
             case kR7: row_tile<R7, ADJ>(a, rec, smem); break;
-            case kR7D: row_tile<R7D, ADJ>(a, rec, smem); break;
             case kR8: row_tile<R8, ADJ>(a, rec, smem); break;
-            case kR8D: row_tile<R8D, ADJ>(a, rec, smem); break;
             case kR8b: row_tile<R8b, ADJ>(a, rec, smem); break;
             case kR9: row_tile<R9, ADJ>(a, rec, smem); break;
-            case kR9D: row_tile<R9D, ADJ>(a, rec, smem); break;
             case kR9b: row_tile<R9b, ADJ>(a, rec, smem); break;
             case kR10: row_tile<R10, ADJ>(a, rec, smem); break;
-            case kR10D: row_tile<R10D, ADJ>(a, rec, smem); break;
             case kR11: row_tile<R11, ADJ>(a, rec, smem); break;
             case kR12: row_tile<R12, ADJ>(a, rec, smem); break;
             default: break;
@@ -383,34 +282,19 @@ template <bool ADJ>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ragged(const RaggedArgs a) {
     extern __shared__ __align__(128) float4 smem4[];
     float* const smem = reinterpret_cast<float*>(smem4);
-    RaggedTail* const tl = tail_of(smem);
-    int4* const s_work = tl->work;
-    uint64_t (&s_bar)[2][2] = tl->bar;
+    int4* const s_work = tail_of(smem)->work;
     const uint32_t rank = cluster_ctarank();
-    const uint32_t b4a = (uint32_t)__cvta_generic_to_shared(&s_bar[0][0]);
-    const uint32_t b4b = (uint32_t)__cvta_generic_to_shared(&s_bar[0][1]);
-    const uint32_t b2a = (uint32_t)__cvta_generic_to_shared(&s_bar[1][0]);
-    const uint32_t b2b = (uint32_t)__cvta_generic_to_shared(&s_bar[1][1]);
-    if (threadIdx.x == 0) {
-        mbar_init(b4a, 4);
-        mbar_init(b4b, 4);
-        mbar_init(b2a, 2);
-        mbar_init(b2b, 2);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    // every CTA of the cluster is running, with its barriers initialised,
-    // before any of its shared memory is accessed from another CTA
+    // every CTA of the cluster is running before any of its shared memory is
+    // accessed from another CTA
     cluster_arrive();
     cluster_wait();
-    if (a.nitems[0] > 0) group_phase<8, 0, ADJ>(a, smem, rank, 0u, 0u);
-    if (a.nitems[1] > 0) group_phase<4, 1, ADJ>(a, smem, rank, b4a, b4b);
-    if (a.nitems[2] > 0) group_phase<2, 2, ADJ>(a, smem, rank, b2a, b2b);
+    if (a.nitems[0] > 0) group_phase<8, 0, ADJ>(a, smem, rank);
+    if (a.nitems[1] > 0) group_phase<4, 1, ADJ>(a, smem, rank);
+    if (a.nitems[2] > 0) group_phase<2, 2, ADJ>(a, smem, rank);
     if (a.nitems[3] > 0) row_phase<ADJ>(a, smem, s_work);
     // No CTA exits while another CTA of its cluster may still read its shared
-    // memory or arrive on its mbarriers.  Group barriers guarantee that on the
-    // normal path; after a wait has given up (SDFT_ERR_TIMEOUT) the CTAs of a
-    // group no longer run in step, and this hardware barrier is what keeps
-    // every CTA's shared memory alive until the whole cluster is done.
+    // memory (the row phase is local, but a CTA whose group phases ended
+    // early must outlive its peers' last remote reads).
     cluster_arrive();
     cluster_wait();
 }

@@ -35,4 +35,14 @@ const KernelInfo* rows_candidate_big(int logn, int idx) {
 #undef SDFT_PICK
 }
 
+// After the prefetching candidates: N = 8192 as 128 threads x 64 values with
+// an XOR-swizzled exchange of exactly 64 KiB, three CTAs per SM (24 K points in
+// flight per SM; measured 285 against 333 Gpts/s for the quarter-row prefetch).
+const KernelInfo* rows_candidate_e64(int logn, int idx) {
+    static const KernelInfo k13 = rows_info<RowCfg<13, 6, 5, 5, 3, 1, 0, 3, false, true>>(
+        "N=8192: 128 threads x 64 values/transform, radix [32,32,8], swizzled exchange, "
+        "three CTAs/SM");
+    return (logn == 13 && idx == 0) ? &k13 : nullptr;
+}
+
 }  // namespace sdft

@@ -27,6 +27,7 @@ const KernelInfo* rows_candidate_small(int logn, int idx);
 const KernelInfo* rows_candidate_1024(int logn, int idx);
 const KernelInfo* rows_candidate_big(int logn, int idx);
 const KernelInfo* rows_pf_candidate(int logn, int idx);
+const KernelInfo* rows_candidate_e64(int logn, int idx);
 
 // The work-queue schedule of a long length: the persistent kernel of ragged
 // plans (ragged.cu) on a uniform batch, with the length's selected form.
@@ -65,11 +66,12 @@ const KernelInfo* f32_candidate(int logn, int idx) {
         return idx >= n ? rows_pf_candidate(logn, idx - n) : nullptr;
     }
     if (logn == 13) {
-        const KernelInfo* k = rows_candidate_big(logn, idx);
-        if (k) return k;
-        int n = 0;
+        int n = 0, m = 0;
         while (rows_candidate_big(logn, n)) ++n;
-        return idx >= n ? rows_pf_candidate(logn, idx - n) : nullptr;
+        while (rows_pf_candidate(logn, m)) ++m;
+        if (idx < n) return rows_candidate_big(logn, idx);
+        if (idx < n + m) return rows_pf_candidate(logn, idx - n);
+        return rows_candidate_e64(logn, idx - n - m);
     }
     if (logn == 14) {
         const KernelInfo* k = rows_candidate_big(logn, idx);
@@ -141,7 +143,6 @@ struct RaggedState {
     int* d_sync = nullptr;             // [claim counters of the phases, a word that stays zero]
     int wait_polls = 1 << 23;          // bound of every device-side wait (polls)
     int inject = 0;                    // tests: group items wait for a word nothing sets
-    unsigned coupled = 0x6u;           // bit p: phase p's groups of a cluster synchronise together
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     cudaGraphNode_t knode[2] = {nullptr, nullptr};
@@ -307,7 +308,6 @@ int launch_ragged(sdft_plan* p, int direction, const float* xr, const float* xi,
     a.status = p->d_status;
     a.wait_polls = r.wait_polls;
     a.inject = r.inject;
-    a.coupled = r.coupled;
     for (int c = 0; c < kRaggedRoutines; ++c) a.tw[c] = r.rtw[c];
     a.w = p->w64;
     void* kargs[] = {&a};
@@ -981,19 +981,6 @@ int sdft_plan_set_ragged_form(sdft_plan* plan, int64_t n, int form) {
         return fail(s);
     }
     return SDFT_OK;
-}
-
-int sdft_plan_set_ragged_coupling(sdft_plan* plan, unsigned mask) {
-    if (!plan_alive(plan)) return fail(SDFT_ERR_BAD_PLAN);
-    if (!plan->rag.on || (mask & ~0x6u) != 0) return fail(SDFT_ERR_INVALID_ARG);
-    plan->rag.coupled = mask;
-    return SDFT_OK;
-}
-
-int sdft_plan_ragged_coupling(const sdft_plan* plan) {
-    if (!plan_alive(plan)) return -fail(SDFT_ERR_BAD_PLAN);
-    if (!plan->rag.on) return -fail(SDFT_ERR_INVALID_ARG);
-    return (int)plan->rag.coupled;
 }
 
 int sdft_plan_ragged_form(const sdft_plan* plan, int64_t n) {

@@ -61,8 +61,6 @@ _SIGS = {
     "sdft_ragged_form_selected": ([_I64], ctypes.c_int),
     "sdft_plan_set_ragged_form": ([_P, _I64, ctypes.c_int], ctypes.c_int),
     "sdft_plan_ragged_form": ([_P, _I64], ctypes.c_int),
-    "sdft_plan_set_ragged_coupling": ([_P, ctypes.c_uint], ctypes.c_int),
-    "sdft_plan_ragged_coupling": ([_P], ctypes.c_int),
     "sdft_plan_ragged_autotune": ([_P, _P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "sdft_plan_inject_unreachable_wait": ([_P, ctypes.c_int], ctypes.c_int),
     "sdft_plan_grid": ([_P], ctypes.c_int),
@@ -230,14 +228,6 @@ def sdft_plan_set_ragged_form(plan, n: int, form: int) -> int:
 
 def sdft_plan_ragged_form(plan, n: int) -> int:
     return lib().sdft_plan_ragged_form(plan, n)
-
-
-def sdft_plan_set_ragged_coupling(plan, mask: int) -> int:
-    return lib().sdft_plan_set_ragged_coupling(plan, mask)
-
-
-def sdft_plan_ragged_coupling(plan) -> int:
-    return lib().sdft_plan_ragged_coupling(plan)
 
 
 def sdft_plan_ragged_autotune(plan, xr, xi, yr, yi, reps: int, stream) -> int:
@@ -431,18 +421,6 @@ class Plan:
 
     def set_ragged_form(self, n: int, form: int) -> None:
         _check(sdft_plan_set_ragged_form(self.handle, n, form), "sdft_plan_set_ragged_form")
-
-    @property
-    def ragged_coupling(self) -> int:
-        """Work-queue plans: bit p set = the groups of phase p (p = 1: 4 CTAs,
-        p = 2: 2 CTAs) of a cluster share the hardware cluster barrier."""
-        v = sdft_plan_ragged_coupling(self.handle)
-        if v < 0:
-            raise SdftError(-v, "sdft_plan_ragged_coupling")
-        return v
-
-    def set_ragged_coupling(self, mask: int) -> None:
-        _check(sdft_plan_set_ragged_coupling(self.handle, mask), "sdft_plan_set_ragged_coupling")
 
     def ragged_autotune(self, xr, xi, yr, yi, reps: int = 10, stream=None) -> int:
         """Time each length's forms on these device tensors (the plan's
