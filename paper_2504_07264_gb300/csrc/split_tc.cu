@@ -236,6 +236,15 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         tc::bulk_g2s(tc::smem_u32(x_re), xr + first * N, bytes, mb_x);
         tc::bulk_g2s(tc::smem_u32(x_im), xi + first * N, bytes, mb_x);
     };
+    // thread 0: the L2 prefetch of tile `t` (its copy into shared memory is
+    // issued later and then reads L2)
+    auto prefetch_tile = [&](long long t) {
+        if (t >= ntiles) return;
+        const long long f2 = t * TPT;
+        const uint32_t b2 = (uint32_t)(((batch - f2 < TPT) ? (batch - f2) : TPT) * N * 4);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(xr + f2 * N), "r"(b2) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(xi + f2 * N), "r"(b2) : "memory");
+    };
     bool x_pending = false;          // thread 0: an input copy not yet waited for
     if (tid == 0) {
         // the block matrices (hi then lo) of this direction and the rotation
@@ -243,7 +252,8 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         tc::mbar_expect_tx(mb_b, 2 * CFG::B_BYTES + CFG::TW_BYTES);
         tc::bulk_g2s(sb_hi, bimg + (ADJ ? CFG::B_BYTES : 0), 2 * CFG::B_BYTES, mb_b);
         tc::bulk_g2s(tc::smem_u32(tw_s), tw + R, CFG::TW_BYTES, mb_b);
-        if (CFG::PREFETCH && blockIdx.x < ntiles) { load_tile(blockIdx.x); x_pending = true; }
+        if (blockIdx.x < ntiles) { load_tile(blockIdx.x); x_pending = true; }
+        if constexpr (!CFG::PREFETCH) prefetch_tile(blockIdx.x + gridDim.x);
     }
     int bad = __syncthreads_or(!tc::mbar_wait(mb_b, 0));
     uint32_t ph_mma = 0, ph_x = 0;
@@ -253,25 +263,11 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
     for (long long tile = blockIdx.x; !bad && tile < ntiles; tile += gridDim.x) {
         const long long first = tile * TPT;
         const long long cnt = (batch - first < TPT) ? (batch - first) : TPT;
-        // the previous tile's output store has finished reading the operand region
-        if (tid == 0) tc::bulk_wait_read0();
-        if constexpr (!CFG::PREFETCH) {
-            __syncthreads();
-            if (tid == 0) {
-                load_tile(tile);
-                x_pending = true;
-                // the next tile into L2 meanwhile: its copy, issued when this
-                // tile's output has left the shared region, then reads L2
-                const long long nx = tile + gridDim.x;
-                if (nx < ntiles) {
-                    const long long f2 = nx * TPT;
-                    const uint32_t b2 = (uint32_t)(((batch - f2 < TPT) ? (batch - f2) : TPT) * N * 4);
-                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
-                                 :: "l"(xr + f2 * N), "r"(b2) : "memory");
-                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
-                                 :: "l"(xi + f2 * N), "r"(b2) : "memory");
-                }
-            }
+        // R = 16: the previous tile's output store has finished reading the
+        // operand region.  (R = 32 stores from registers; its input copy was
+        // issued when the previous tile's GEMM 2 completed.)
+        if constexpr (CFG::PREFETCH) {
+            if (tid == 0) tc::bulk_wait_read0();
         }
         if (__syncthreads_or(!tc::mbar_wait(mb_x, ph_x))) { bad = 1; break; }
         ph_x ^= 1;
@@ -330,24 +326,49 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         if (__syncthreads_or(!tc::mbar_wait(mb_mma, ph_mma))) { bad = 1; break; }
         ph_mma ^= 1;
         tc::fence_after_sync();
-        // ---- row (b, d): y[d + R * k2] for every k2, scales undone, via a
-        // shared output tile and one bulk store per plane
-        float d2[2 * R];
-        tmem_row<R>(lane_base + NM, d2);
-        tc::fence_before_sync();
         const float us = ldexpf(1.f, e0 + e1);
+        float d2[2 * R];
+        if constexpr (!CFG::PREFETCH) {
+            // R = 32: GEMM 2 has read the operand region, nothing else will:
+            // the next tile's input copy starts now (and the one after it into
+            // L2), overlapping this tile's TMEM reads and stores
+            if (tid == 0 && tile + gridDim.x < ntiles) {
+                load_tile(tile + gridDim.x);
+                x_pending = true;
+                prefetch_tile(tile + 2 * gridDim.x);
+            }
+            // ---- row (b, d): y[d + R * k2] for every k2, scales undone, straight
+            // from registers (a warp is one transform's 32 digits d: every
+            // store is one whole 128-byte line)
+            tmem_row<R>(lane_base + NM, d2);
+            tc::fence_before_sync();
+            if (bl < cnt) {
+                float* const gyr = yr + (first + bl) * N + c;
+                float* const gyi = yi + (first + bl) * N + c;
 #pragma unroll
-        for (int k2 = 0; k2 < R; ++k2) {
-            y_re[bl * N + c + R * k2] = d2[k2] * us;
-            y_im[bl * N + c + R * k2] = d2[R + k2] * us;
-        }
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t bytes = (uint32_t)(cnt * N * 4);
-            tc::bulk_s2g(yr + first * N, tc::smem_u32(y_re), bytes);
-            tc::bulk_s2g(yi + first * N, tc::smem_u32(y_im), bytes);
-            tc::bulk_commit();
+                for (int k2 = 0; k2 < R; ++k2) {
+                    gyr[R * k2] = d2[k2] * us;
+                    gyi[R * k2] = d2[R + k2] * us;
+                }
+            }
+        } else {
+            // ---- row (b, d): y[d + R * k2] for every k2, scales undone, via a
+            // shared output tile and one bulk store per plane
+            tmem_row<R>(lane_base + NM, d2);
+            tc::fence_before_sync();
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) {
+                y_re[bl * N + c + R * k2] = d2[k2] * us;
+                y_im[bl * N + c + R * k2] = d2[R + k2] * us;
+            }
+            tc::fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                const uint32_t bytes = (uint32_t)(cnt * N * 4);
+                tc::bulk_s2g(yr + first * N, tc::smem_u32(y_re), bytes);
+                tc::bulk_s2g(yi + first * N, tc::smem_u32(y_im), bytes);
+                tc::bulk_commit();
+            }
         }
     }
     if (tid == 0) {
