@@ -55,9 +55,11 @@ __device__ __forceinline__ void cluster_wait() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 // the address of the same shared-memory location in CTA `rank` of the cluster
+// (a pure function of its operands: not volatile, so equal mappings are
+// computed once)
 __device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
     uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
     return r;
 }
 // Bring `bytes` (a multiple of 16, 16-byte aligned) of global memory into L2,
@@ -202,11 +204,17 @@ __device__ __forceinline__ void pass2(ST st, float* const work, const uint32_t y
     const int sub2 = tid % AQ, tc = tid / AQ;
     float* const x_re = work;                 // exchange [L][sub2]
     float* const x_im = work + C * AQ;
-    // column L of row d lives in CTA L / CQ at Y[L % CQ][d]
+    // Column L of row d lives in CTA L / CQ at Y[L % CQ][d].  A step-0
+    // element is L = c0 + C_s * i with c0 = tc + T * f < C_s <= CQ, so its
+    // column is tc + ((L - tc) % CQ) and its CTA (L - tc) / CQ: L - tc is a
+    // compile-time constant, and the address depends on the thread only
+    // through tc and d (a few distinct bases, shared by many elements).
+    static_assert((CFG::C >> SC::lr(0)) <= CQ, "a step-0 column stays within one CTA's columns");
     auto ld = [&](int L, float& r, float& i) {
-        const int c = L & (CQ - 1);
+        const int k = L - tc;
+        const int c = tc + (k & (CQ - 1));
         const uint32_t a = map_rank(y_sh + 4u * (uint32_t)(c * A + (d ^ CFG::swz(c))),
-                                    rank0 + (uint32_t)(L >> CFG::LOGCQ));
+                                    rank0 + (uint32_t)(k >> CFG::LOGCQ));
         r = ld_cluster(a);
         i = ld_cluster(a + 4u * (uint32_t)(A * CQ));
     };
