@@ -624,7 +624,17 @@ def ragged_block(steps: int, warmup: int, stream, tune: bool = True) -> dict:
     line = {}
     with Plan(lengths=lengths) as plan:
         if tune:
-            # each length's form, chosen on this batch by the plan's tuner
+            # every length on its form 0 first (the library's default), then
+            # each length's form chosen on this batch by the plan's tuner
+            for logn in range(2, 17):
+                if (lengths == (1 << logn)).any():
+                    plan.set_ragged_form(1 << logn, 0)
+            fwd0 = lambda: plan.execute(SDFT_FORWARD, xr, xi, yr, yi, stream)  # noqa: E731
+            for _ in range(warmup):
+                fwd0()
+            ms0 = _time_steps(fwd0, steps, stream)
+            line["default_forms"] = {"gpts": points / (ms0 * 1e-3) / 1e9, "ms": ms0,
+                                     "what": "forward, every length on its form 0, before tuning"}
             line["ragged_tuning"] = plan.ragged_autotune(xr, xi, yr, yi, reps=5, stream=stream)
         line["forms"] = {str(1 << l): plan.ragged_form(1 << l)
                          for l in range(2, 17) if (lengths == (1 << l)).any()}
@@ -680,6 +690,8 @@ def ragged_block(steps: int, warmup: int, stream, tune: bool = True) -> dict:
         "gpts": points / (ms_u * 1e-3) / 1e9, "ms": ms_u, "gbs": gbs, "frac": gbs / peak,
         "launches": len(plans), "what": "one uniform FP32 plan per length, data pre-sorted"}
     line["vs_per_length_uniform"] = line["forward"]["gpts"] / line["per_length_uniform_kernels"]["gpts"]
+    if "default_forms" in line:
+        line["tuned_vs_default_forms"] = line["forward"]["gpts"] / line["default_forms"]["gpts"]
     line["points"] = points
     line["workload"] = (f"batching: {lengths.size} transforms, lengths 2^U{{3..16}} (seed 4), "
                         f"{points} points, iid N(0,1); one persistent launch in a CUDA graph")
