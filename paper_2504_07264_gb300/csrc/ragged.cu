@@ -65,12 +65,12 @@ const FormTable& forms() {
         add(row_form<R9>("N=512: tile of 8 transforms, 16 threads each, radix [32,16]", kR9));
         add(row_form<R9b>("N=512: tile of 4 transforms, 32 threads each, radix [16,16,2]", kR9b));
         add(row_form<R10>("N=1024: tile of 4 transforms, 32 threads each, radix [32,32]", kR10));
+        add(row_form<R10b>("N=1024: tile of 2 transforms, 64 threads each, radix [16,8,8]", kR10b));
         add(row_form<R11>("N=2048: tile of 2 transforms, 64 threads each, radix [32,16,4]", kR11));
+        add(row_form<R11b>("N=2048: tile of 1 transform, 128 threads, radix [16,16,8]", kR11b));
         add(row_form<R12>("N=4096: tile of 1 transform, 128 threads, radix [32,32,4]", kR12));
         add(group_form<Cluster13>("N=8192: 2 CTAs per transform, distributed shared memory, 128 x 64", kC13));
-        add(group_form<Cluster14e>("N=16384: 2 CTAs x 64 values per thread, distributed shared memory, 128 x 128", kC14e));
         add(group_form<Cluster14q>("N=16384: 4 CTAs x 32 values per thread, distributed shared memory, 128 x 128", kC14q));
-        add(group_form<Cluster15e>("N=32768: 4 CTAs x 64 values per thread, distributed shared memory, 256 x 128", kC15e));
         add(group_form<Cluster15q>("N=32768: 8 CTAs x 32 values per thread, distributed shared memory, 256 x 128", kC15q));
         add(group_form<Cluster16e>("N=65536: 8 CTAs x 64 values per thread, distributed shared memory, 256 x 256", kC16e));
         return x;

@@ -60,13 +60,15 @@ using R8b = RowCfg<8, 5, 5, 3, 0, 16, 8>;           // 8 threads x 32 values, ra
 using R9 = RowCfg<9, 5, 5, 4, 0, 8, 16>;
 using R9b = RowCfg<9, 4, 4, 4, 1, 4>;               // 32 threads, radix [16,16,2]
 using R10 = RowCfg<10, 5, 5, 5, 0, 4>;
+using R10b = RowCfg<10, 4, 4, 3, 3, 2>;             // 64 threads, radix [16,8,8]
 using R11 = RowCfg<11, 5, 5, 4, 2, 2>;              // 64 threads, radix [32,16,4]
+using R11b = RowCfg<11, 4, 4, 4, 3, 1>;             // 128 threads, radix [16,16,8]
 using R12 = RowCfg<12, 5, 5, 5, 2, 1>;              // 128 threads, radix [32,32,4]
 
 // routine codes (the first word of every work item)
 enum : int {
-    kR2, kR3, kR4, kR5, kR6, kR7, kR8, kR8b, kR9, kR9b, kR10, kR11, kR12,
-    kC13, kC14e, kC14q, kC15e, kC15q, kC16e, kRoutineCount
+    kR2, kR3, kR4, kR5, kR6, kR7, kR8, kR8b, kR9, kR9b, kR10, kR10b, kR11, kR11b, kR12,
+    kC13, kC14q, kC15q, kC16e, kRoutineCount
 };
 static_assert(kRoutineCount <= kRaggedRoutines, "routine table");
 
@@ -91,9 +93,8 @@ struct RaggedTail {
 // CTAs: a one-CTA tile of it, 128 threads x 64 values with an XOR-swizzled
 // exchange of exactly 64 KiB, measured 145 against 152 Gpts/s.)
 constexpr size_t kData = smax(
-    smax(smax(R9::SMEM, R10::SMEM), smax(R11::SMEM, R12::SMEM)),
-    smax(smax(smax(Cluster13::SMEM, Cluster14e::SMEM), smax(Cluster14q::SMEM, Cluster15e::SMEM)),
-         smax(Cluster15q::SMEM, Cluster16e::SMEM)));
+    smax(smax(R9::SMEM, R10::SMEM), smax(smax(R10b::SMEM, R11::SMEM), smax(R11b::SMEM, R12::SMEM))),
+    smax(smax(Cluster13::SMEM, Cluster14q::SMEM), smax(Cluster15q::SMEM, Cluster16e::SMEM)));
 static_assert(kData <= 64 * 1024, "three CTAs per SM within the 196 KiB carveout");
 constexpr size_t kSmem = kData + ((sizeof(RaggedTail) + 127) / 128) * 128;
 static_assert(kData % 128 == 0, "the tail starts 128-byte aligned");
@@ -216,9 +217,7 @@ __device__ __forceinline__ void group_phase(const RaggedArgs& a, float* smem, co
         switch (rec.x) {
             case kC16e: if constexpr (Q == 8) group_item<Cluster16e, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
             case kC15q: if constexpr (Q == 8) group_item<Cluster15q, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
-            case kC15e: if constexpr (Q == 4) group_item<Cluster15e, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
             case kC14q: if constexpr (Q == 4) group_item<Cluster14q, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
-            case kC14e: if constexpr (Q == 2) group_item<Cluster14e, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
             case kC13: if constexpr (Q == 2) group_item<Cluster13, ADJ>(a, rec, smem, q, g0, mid, sync, rd); break;
             default:   // no transform for this group in this round: the barriers only
                 if (threadIdx.x == 0) tl->next[par] = nxt;
@@ -269,7 +268,9 @@ __device__ __forceinline__ void row_phase(const RaggedArgs& a, float* smem, int4
             case kR9: row_tile<R9, ADJ>(a, rec, smem); break;
             case kR9b: row_tile<R9b, ADJ>(a, rec, smem); break;
             case kR10: row_tile<R10, ADJ>(a, rec, smem); break;
+            case kR10b: row_tile<R10b, ADJ>(a, rec, smem); break;
             case kR11: row_tile<R11, ADJ>(a, rec, smem); break;
+            case kR11b: row_tile<R11b, ADJ>(a, rec, smem); break;
             case kR12: row_tile<R12, ADJ>(a, rec, smem); break;
             default: break;
         }

@@ -106,8 +106,9 @@ def test_ragged_forms_catalogue():
         for f in range(c):
             assert S.sdft_ragged_form_describe(n, f).startswith(f"N={n}:")
         assert S.lib().sdft_ragged_form_describe(n, c, None, 0) == -S.SDFT_ERR_INVALID_ARG
-    # the long lengths offer several CTA counts, the autotuner's choice
-    assert S.sdft_ragged_form_count(16384) >= 2 and S.sdft_ragged_form_count(32768) >= 2
+    # lengths with a choice of radix split and tile size for the plan tuner
+    for n in (256, 512, 1024, 2048):
+        assert S.sdft_ragged_form_count(n) >= 2
     for n in (2, 3, 131072):
         assert S.sdft_ragged_form_count(n) == -S.SDFT_ERR_UNSUPPORTED_N
     assert S.lib().sdft_ragged_form_select(1024, 99) == S.SDFT_ERR_INVALID_ARG

@@ -83,8 +83,9 @@ def test_every_class_and_many_items():
 
 
 # uniform-plan schedule with the same arithmetic as the ragged kernel's form 0
-# (the same radix split and tables; for N >= 16384 the 64-value cluster kernel)
-SAME_SCHEDULE = {16: 0, 1024: 0, 4096: 0, 16384: 5, 32768: 4, 65536: 3}
+# (the same radix split and tables; for N >= 16384 a cluster kernel with the
+# same A x C split, whatever its number of CTAs)
+SAME_SCHEDULE = {16: 0, 1024: 0, 4096: 0, 16384: 3, 32768: 3, 65536: 3}
 
 
 def test_matches_uniform_plans_bitwise():
@@ -255,13 +256,11 @@ def test_groups_of_every_size_in_one_launch():
                               ((65536, 45), (32768, 70), (16384, 150), (8192, 200), (512, 900))])
     lengths = rng.permutation(lengths)
     xr, xi, off = _ragged_inputs(lengths, 49)
-    # N = 32768 on four CTAs (form 0) or eight (1); 16384 on two (0) or four
-    # (1); 8192 on two CTAs
-    for f15, f14, f13 in ((0, 0, 0), (1, 1, 0), (0, 1, 0)):
+    # N = 65536 and 32768 on eight CTAs, 16384 on four, 8192 on two; 512 in
+    # each of its row forms
+    for f9 in range(S.sdft_ragged_form_count(512)):
         with Plan(lengths=lengths) as plan:
-            plan.set_ragged_form(32768, f15)
-            plan.set_ragged_form(16384, f14)
-            plan.set_ragged_form(8192, f13)
+            plan.set_ragged_form(512, f9)
             for direction in (0, 1):
                 yr, yi = _run(plan, xr, xi, direction)
                 assert plan.sync_status() == S.SDFT_OK

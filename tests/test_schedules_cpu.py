@@ -75,16 +75,16 @@ def test_ragged_forms_save_apply(tmp_path):
     """The work-queue forms are kept beside the schedules and applied as the
     process-wide choice for later ragged plans."""
     path = str(tmp_path / "tune.json")
-    A.save({"ragged": {"32768": 1, "16384": 1}}, path, name="Test GPU")
+    A.save({"ragged": {"512": 1, "1024": 1}}, path, name="Test GPU")
     A.save({"0": {"4096": {"index": 0, "ms": [0.1], "schedules": ["a"]}}}, path, name="Test GPU")
     table = A.load(path)
-    assert table["Test GPU"]["ragged"] == {"32768": 1, "16384": 1}
+    assert table["Test GPU"]["ragged"] == {"512": 1, "1024": 1}
     try:
         assert A.apply(table, name="Test GPU") == 3
-        assert S.sdft_ragged_form_selected(32768) == 1
-        assert S.sdft_ragged_form_selected(16384) == 1
+        assert S.sdft_ragged_form_selected(512) == 1
+        assert S.sdft_ragged_form_selected(1024) == 1
     finally:
-        S.lib().sdft_ragged_form_select(32768, 0)
-        S.lib().sdft_ragged_form_select(16384, 0)
+        S.lib().sdft_ragged_form_select(512, 0)
+        S.lib().sdft_ragged_form_select(1024, 0)
     # an out-of-range form in a table is skipped, not applied
     assert A.apply({"G": {"ragged": {"65536": 7}}}, name="G") == 0
