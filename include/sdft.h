@@ -193,6 +193,17 @@ SDFT_API int sdft_ragged_form_selected(int64_t n);
 SDFT_API int sdft_plan_set_ragged_form(sdft_plan* plan, int64_t n, int form);
 /* The form length n runs in on this plan (>= 0), or -status. */
 SDFT_API int sdft_plan_ragged_form(const sdft_plan* plan, int64_t n);
+/* Host-only view of the work a ragged plan of these lengths (as for
+ * sdft_plan_create_ragged) would run with the process-wide forms, without
+ * touching any GPU: for every transform t, phase_of[t] (0, 1, 2: a transform
+ * held by 8, 4 or 2 CTAs; 3: a row tile) and item_of[t] (its work item within
+ * that phase); nitems[0..3] receives the number of items of each phase.  Items
+ * of a phase are ordered longest transforms first; a group item holds one
+ * transform, a row tile up to the form's transforms per tile, all of one
+ * length.  phase_of and item_of have room for `count` entries.  Returns
+ * SDFT_OK, SDFT_ERR_INVALID_ARG or SDFT_ERR_UNSUPPORTED_N. */
+SDFT_API int sdft_ragged_work_layout(const int64_t* lengths, int64_t count, int32_t* phase_of,
+                                     int32_t* item_of, int64_t* nitems);
 /* Autotune a work-queue plan on the caller's device buffers (the plan's
  * layout, read xr/xi, written yr/yi): one length at a time, longest first,
  * time the plan's forward call with each form of that length (`reps` timed

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <new>
 #include <set>
+#include <utility>
 #include <vector>
 
 #include "../../include/sdft.h"
@@ -369,46 +370,74 @@ int run(sdft_plan* p, int direction, const float* xr, const float* xi, float* yr
     return launch(p, direction, xr, xi, yr, yi, stream, batch, scratch);
 }
 
-// Work items of a work-queue plan under its current forms (ragged.h): one
-// item per transform for the group phases (q = 8, 4, 2), longest first; row
-// tiles of `per_item` transforms for q = 1, longest first.  Uploads them on
-// `st` (the caller synchronises).
-int build_queue(sdft_plan* p, cudaStream_t st) {
-    RaggedState& r = p->rag;
+// Work items of a work-queue plan (host only): for transforms of log2 lengths
+// logn[] starting at start[] (floats) and the form of every length, one item
+// per transform for the group phases (q = 8, 4, 2), longest first, and row
+// tiles of `per_item` transforms for q = 1, longest first (ragged.h).
+// `owner[t]` records (phase, item) of transform t.
+struct RaggedWork {
     std::vector<int4> items[kRaggedPhases];
-    std::vector<long long> order_off;
+    std::vector<long long> order_off;            // row tiles: row starts in work order
+    std::vector<std::pair<int, int>> owner;      // per transform: (phase, item)
+};
+
+int ragged_work(const signed char* logn, const long long* start, int64_t count,
+                const int* form, RaggedWork& w) {
+    unsigned classes = 0;
+    for (int64_t t = 0; t < count; ++t) classes |= 1u << logn[t];
+    w.owner.assign((size_t)count, std::make_pair(-1, -1));
     for (int l = kMaxLogN; l >= 2; --l) {
-        if (!(r.classes & (1u << l))) continue;
-        const RaggedForm* f = ragged_form(l, r.form[l]);
+        if (!(classes & (1u << l))) continue;
+        const RaggedForm* f = ragged_form(l, form[l]);
         if (!f) return SDFT_ERR_INVALID_ARG;
         const int ph = ragged_phase_of(f->q);
         if (f->q > 1) {
-            for (int64_t t = 0; t < r.count; ++t)
-                if (r.logn[(size_t)t] == l) {
-                    const long long o = r.start[(size_t)t];
-                    items[ph].push_back(make_int4(f->code, (int)(uint32_t)o,
-                                                  (int)(uint32_t)((unsigned long long)o >> 32),
-                                                  1 << l));
+            for (int64_t t = 0; t < count; ++t)
+                if (logn[t] == l) {
+                    const long long o = start[t];
+                    w.owner[(size_t)t] = std::make_pair(ph, (int)w.items[ph].size());
+                    w.items[ph].push_back(make_int4(f->code, (int)(uint32_t)o,
+                                                    (int)(uint32_t)((unsigned long long)o >> 32),
+                                                    1 << l));
                 }
         } else {
-            const int first = (int)order_off.size();
-            for (int64_t t = 0; t < r.count; ++t)
-                if (r.logn[(size_t)t] == l) order_off.push_back(r.start[(size_t)t]);
-            const int n_in = (int)order_off.size() - first;
+            const int first = (int)w.order_off.size();
+            for (int64_t t = 0; t < count; ++t)
+                if (logn[t] == l) {
+                    w.owner[(size_t)t] = std::make_pair(
+                        ph, (int)w.items[ph].size() + ((int)w.order_off.size() - first) / f->per_item);
+                    w.order_off.push_back(start[t]);
+                }
+            const int n_in = (int)w.order_off.size() - first;
             for (int s0 = 0; s0 < n_in; s0 += f->per_item)
-                items[ph].push_back(make_int4(f->code, first + s0, std::min(f->per_item, n_in - s0), 0));
+                w.items[ph].push_back(make_int4(f->code, first + s0, std::min(f->per_item, n_in - s0), 0));
         }
     }
+    for (int ph = 0; ph < kRaggedPhases; ++ph)
+        if ((int64_t)w.items[ph].size() > count) return SDFT_ERR_INVALID_ARG;
+    return SDFT_OK;
+}
+
+// Upload a work-queue plan's items under its current forms on `st` (the
+// caller synchronises).
+int build_queue(sdft_plan* p, cudaStream_t st) {
+    RaggedState& r = p->rag;
+    RaggedWork w;
+    try {
+        const int s = ragged_work(r.logn.data(), r.start.data(), r.count, r.form, w);
+        if (s != SDFT_OK) return s;
+    } catch (...) {
+        return SDFT_ERR_ALLOC;
+    }
     for (int ph = 0; ph < kRaggedPhases; ++ph) {
-        if ((int64_t)items[ph].size() > r.count) return SDFT_ERR_INVALID_ARG;
-        if (!items[ph].empty() &&
-            cudaMemcpyAsync(r.d_items[ph], items[ph].data(), items[ph].size() * sizeof(int4),
+        if (!w.items[ph].empty() &&
+            cudaMemcpyAsync(r.d_items[ph], w.items[ph].data(), w.items[ph].size() * sizeof(int4),
                             cudaMemcpyHostToDevice, st) != cudaSuccess)
             return SDFT_ERR_CUDA;
-        r.nitems[ph] = (int)items[ph].size();
+        r.nitems[ph] = (int)w.items[ph].size();
     }
-    if (!order_off.empty() &&
-        cudaMemcpyAsync(r.d_offsets, order_off.data(), order_off.size() * sizeof(long long),
+    if (!w.order_off.empty() &&
+        cudaMemcpyAsync(r.d_offsets, w.order_off.data(), w.order_off.size() * sizeof(long long),
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
         return SDFT_ERR_CUDA;
     return SDFT_OK;
@@ -979,6 +1008,38 @@ int sdft_plan_set_ragged_form(sdft_plan* plan, int64_t n, int form) {
         r.form[l] = prev;
         rebuild_queue(plan);
         return fail(s);
+    }
+    return SDFT_OK;
+}
+
+int sdft_ragged_work_layout(const int64_t* lengths, int64_t count, int32_t* phase_of,
+                            int32_t* item_of, int64_t* nitems) {
+    if (lengths == nullptr || count < 1 || count > ((int64_t)1 << 31) || !phase_of || !item_of ||
+        !nitems)
+        return fail(SDFT_ERR_INVALID_ARG);
+    try {
+        std::vector<signed char> logn((size_t)count);
+        std::vector<long long> start((size_t)count);
+        long long total = 0;
+        for (int64_t t = 0; t < count; ++t) {
+            const int l = log2_exact(lengths[t]);
+            if (l < 2 || l > kMaxLogN) return fail(SDFT_ERR_UNSUPPORTED_N);
+            logn[(size_t)t] = (signed char)l;
+            start[(size_t)t] = total;
+            total += lengths[t];
+        }
+        int form[17] = {};
+        for (int l = 2; l <= kMaxLogN; ++l) form[l] = g_rform[l].load();
+        RaggedWork w;
+        const int s = ragged_work(logn.data(), start.data(), count, form, w);
+        if (s != SDFT_OK) return fail(s);
+        for (int64_t t = 0; t < count; ++t) {
+            phase_of[t] = w.owner[(size_t)t].first;
+            item_of[t] = w.owner[(size_t)t].second;
+        }
+        for (int ph = 0; ph < kRaggedPhases; ++ph) nitems[ph] = (int64_t)w.items[ph].size();
+    } catch (...) {
+        return fail(SDFT_ERR_ALLOC);
     }
     return SDFT_OK;
 }

@@ -61,6 +61,7 @@ _SIGS = {
     "sdft_ragged_form_selected": ([_I64], ctypes.c_int),
     "sdft_plan_set_ragged_form": ([_P, _I64, ctypes.c_int], ctypes.c_int),
     "sdft_plan_ragged_form": ([_P, _I64], ctypes.c_int),
+    "sdft_ragged_work_layout": ([_P, _I64, _P, _P, _P], ctypes.c_int),
     "sdft_plan_ragged_autotune": ([_P, _P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "sdft_plan_inject_unreachable_wait": ([_P, ctypes.c_int], ctypes.c_int),
     "sdft_plan_grid": ([_P], ctypes.c_int),
@@ -228,6 +229,21 @@ def sdft_plan_set_ragged_form(plan, n: int, form: int) -> int:
 
 def sdft_plan_ragged_form(plan, n: int) -> int:
     return lib().sdft_plan_ragged_form(plan, n)
+
+
+def sdft_ragged_work_layout(lengths):
+    """(phase_of, item_of, nitems) for a ragged batch of these lengths with the
+    process-wide forms (host only; see include/sdft.h)."""
+    import numpy as np
+    arr = np.ascontiguousarray(lengths, dtype=np.int64)
+    phase = np.empty(arr.size, dtype=np.int32)
+    item = np.empty(arr.size, dtype=np.int32)
+    nitems = np.zeros(4, dtype=np.int64)
+    st = lib().sdft_ragged_work_layout(arr.ctypes.data, arr.size, phase.ctypes.data,
+                                       item.ctypes.data, nitems.ctypes.data)
+    if st != SDFT_OK:
+        raise SdftError(st, "sdft_ragged_work_layout")
+    return phase, item, nitems
 
 
 def sdft_plan_ragged_autotune(plan, xr, xi, yr, yi, reps: int, stream) -> int:

@@ -113,3 +113,64 @@ def test_ragged_forms_catalogue():
         assert S.sdft_ragged_form_count(n) == -S.SDFT_ERR_UNSUPPORTED_N
     assert S.lib().sdft_ragged_form_select(1024, 99) == S.SDFT_ERR_INVALID_ARG
     assert S.lib().sdft_ragged_form_select(2, 0) == S.SDFT_ERR_UNSUPPORTED_N
+
+
+def _layout_invariants(lengths):
+    import numpy as np
+    phase, item, nitems = S.sdft_ragged_work_layout(lengths)
+    n = len(lengths)
+    assert phase.shape == (n,) and ((phase >= 0) & (phase <= 3)).all()
+    for ph in range(4):
+        sel = np.nonzero(phase == ph)[0]
+        if ph < 3:
+            # one transform per group item, every item used once, and the CTAs
+            # per transform of the form match the phase (8, 4, 2)
+            assert sorted(item[sel]) == list(range(nitems[ph]))
+            q = {0: 8, 1: 4, 2: 2}[ph]
+            for t in sel:
+                f = S.sdft_ragged_form_selected(int(lengths[t]))
+                assert f"{q} CTAs" in S.sdft_ragged_form_describe(int(lengths[t]), f)
+        else:
+            assert set(item[sel]) == set(range(nitems[3]))
+            for it in range(nitems[3]):
+                members = lengths[sel[item[sel] == it]]
+                assert members.size >= 1 and (members == members[0]).all()
+        # items of a phase are ordered longest transforms first
+        if sel.size:
+            first_len = [lengths[sel[item[sel] == it][0]] for it in range(nitems[ph])]
+            assert all(a >= b for a, b in zip(first_len, first_len[1:]))
+    return phase, item, nitems
+
+
+def test_ragged_work_layout_host_logic():
+    """The ragged plan's work items, computed on the host (no GPU): every
+    transform in exactly one item of the phase its length's form puts it in,
+    group items one transform each, row tiles of one length, longest first."""
+    import numpy as np
+    rng = np.random.default_rng(60)
+    for trial in range(5):
+        lengths = (1 << rng.integers(2, 17, size=300 + 100 * trial)).astype(np.int64)
+        _layout_invariants(lengths)
+    # the benchmark's workload: lengths 2^U{3..16}, seed 4
+    import workloads
+    cfg = workloads.RAGGED
+    lengths, _ = workloads.ragged_lengths(cfg["count"], cfg["kmin"], cfg["kmax"], cfg["seed"])
+    phase, item, nitems = _layout_invariants(lengths)
+    assert nitems.sum() == (phase < 3).sum() + nitems[3]
+
+
+def test_ragged_work_layout_follows_forms_and_rejects_bad_lengths():
+    import numpy as np
+    lengths = np.array([512] * 20 + [8192, 4], dtype=np.int64)
+    try:
+        for f in range(S.sdft_ragged_form_count(512)):
+            assert S.lib().sdft_ragged_form_select(512, f) == S.SDFT_OK
+            per = int(S.sdft_ragged_form_describe(512, f).split("tile of ")[1].split()[0])
+            phase, item, nitems = _layout_invariants(lengths)
+            rows512 = item[(lengths == 512)]
+            assert len(set(rows512)) == -(-20 // per)
+    finally:
+        S.lib().sdft_ragged_form_select(512, 0)
+    for bad in ([8, 12], [2], [1 << 17]):
+        with pytest.raises(S.SdftError):
+            S.sdft_ragged_work_layout(np.asarray(bad, dtype=np.int64))
