@@ -3,7 +3,9 @@
 // padded shared-memory exchange between the two register steps.  (Measured and
 // left out: 16 threads x 64 values per transform, eight transforms per CTA of
 // 128 threads, three CTAs per SM on a 64 KiB XOR-swizzled exchange whose
-// rotation flips by 16 banks for odd transforms: 297 against 402 Gpts/s.)
+// rotation flips by 16 banks for odd transforms: 297 against 402 Gpts/s; and
+// candidate 0 with thread 0 bringing the CTA's next tile into L2 by two bulk
+// prefetches at the top of each tile: 325 against 402.)
 #include "kernels_rows.cuh"
 
 namespace sdft {
