@@ -42,3 +42,12 @@ def test_warmup_contract():
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                         "--steps", "1", "--warmup", "1"], capture_output=True, text=True)
     assert p.returncode != 0 and "--warmup must be >= 3" in p.stderr
+
+
+def test_source_hash_ignores_comments_only():
+    a = "int f(int x) { return x + 1; }  // one\n/* two */"
+    b = "/* another */ int f(int x)\n{ return x + 1; } // three"
+    c = "int f(int x) { return x + 2; }"
+    assert bench._code_only(a) == bench._code_only(b) != bench._code_only(c)
+    # the stored traffic figure belongs to the kernel as it is
+    assert bench._kernel_source_hash() == bench.NCU_TRAFFIC["fwd"]["hash"]
