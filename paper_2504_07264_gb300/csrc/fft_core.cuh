@@ -12,7 +12,7 @@
 // DFTs over the remaining digits (the same butterfly W(i) and rotation D(i)
 // factors of Eq. (6), applied in decimation-in-frequency order, cf. Eq. (9)).
 // Each "step" below is one such regrouping: every thread runs small DFTs
-// entirely in registers (radix-2 DIF butterflies with compile-time rotation
+// entirely in registers (split-radix DIF butterflies with compile-time rotation
 // constants), then rotates by per-plan twiddle tables, then exchanges data
 // through shared memory for the next step.  The final step writes natural
 // order, so the permutation S of Eq. (6) never materialises: it is absorbed
@@ -88,30 +88,97 @@ __device__ __forceinline__ void rot(float& r, float& i, const float2 w) {
     i = ni;
 }
 
+// (r + j i) <- (r + j i) * W_L^q (conjugate for the adjoint) for a
+// compile-time q anywhere on the circle, 0 <= q < L <= 64: the quarter turns
+// and the odd eighths written out, the rest from the W_64 constants.
+template <bool ADJ>
+__device__ __forceinline__ void rot_any(float& r, float& i, const int q, const int L,
+                                        const W64& w) {
+    if (q == 0) return;
+    if (2 * q == L) {                      // -1
+        r = -r;
+        i = -i;
+        return;
+    }
+    if (4 * q == L || 4 * q == 3 * L) {    // -j, or +j for three quarters (conjugated: adjoint)
+        const bool minus_j = (4 * q == L) != ADJ;
+        const float a = r;
+        if (minus_j) { r = i; i = -a; } else { r = -i; i = a; }
+        return;
+    }
+    if ((8 * q) % L == 0) {                // odd eighths: (+-1 +- j)/sqrt2
+        const float h = 0.70710678118654752440f;
+        const int m = 8 * q / L;           // W_8^m, m = 1, 3, 5, 7
+        const float c = (m == 1 || m == 7) ? h : -h;
+        const float sf = (m == 1 || m == 3) ? -h : h;
+        const float sv = ADJ ? -sf : sf;
+        const float a = r, b = i;
+        r = a * c - b * sv;
+        i = a * sv + b * c;
+        return;
+    }
+    const int idx = q * (64 / L);
+    const float c = w.c[idx];
+    const float sv = ADJ ? -w.s[idx] : w.s[idx];
+    const float nr = r * c - i * sv;
+    const float ni = r * sv + i * c;
+    r = nr;
+    i = ni;
+}
+
+// In-register L-point DFT of re/im[off .. off+L-1] (natural input order) by
+// split-radix decimation in frequency: with t1 = x_n - x_{n+L/2} and
+// t2 = x_{n+L/4} - x_{n+3L/4} (n < L/4),
+//   first half     x_n + x_{n+L/2}            -> the L/2-point DFT: X[2k]
+//   third quarter  (t1 - j t2) W_L^n          -> L/4-point DFT:     X[4k+1]
+//   fourth quarter (t1 + j t2) W_L^{3n}       -> L/4-point DFT:     X[4k+3]
+// (+j and -j exchanged, rotations conjugated, for the adjoint).  These are the
+// radix-2 factors W(i) and D(i) of Eq. (6) regrouped so that two stages share
+// one rotation; bin k lands in register off + brevc(k, log2 L), the order the
+// radix-2 form gives.
+template <int L, bool ADJ, int E>
+__device__ __forceinline__ void dft_split_radix(float (&re)[E], float (&im)[E], const int off,
+                                                const W64& w) {
+    if constexpr (L == 2) {
+        const float ur = re[off], ui = im[off], vr = re[off + 1], vi = im[off + 1];
+        re[off] = ur + vr;
+        im[off] = ui + vi;
+        re[off + 1] = ur - vr;
+        im[off + 1] = ui - vi;
+    } else if constexpr (L >= 4) {
+        constexpr int Q = L / 4;
+#pragma unroll
+        for (int n = 0; n < Q; ++n) {
+            const int a = off + n, b = a + Q, c = b + Q, d = c + Q;
+            const float t1r = re[a] - re[c], t1i = im[a] - im[c];
+            const float t2r = re[b] - re[d], t2i = im[b] - im[d];
+            re[a] += re[c];
+            im[a] += im[c];
+            re[b] += re[d];
+            im[b] += im[d];
+            // forward: z1 = t1 - j t2, z3 = t1 + j t2
+            float z1r = ADJ ? t1r - t2i : t1r + t2i, z1i = ADJ ? t1i + t2r : t1i - t2r;
+            float z3r = ADJ ? t1r + t2i : t1r - t2i, z3i = ADJ ? t1i - t2r : t1i + t2r;
+            rot_any<ADJ>(z1r, z1i, n, L, w);
+            rot_any<ADJ>(z3r, z3i, 3 * n, L, w);
+            re[c] = z1r;
+            im[c] = z1i;
+            re[d] = z3r;
+            im[d] = z3i;
+        }
+        dft_split_radix<L / 2, ADJ>(re, im, off, w);
+        dft_split_radix<L / 4, ADJ>(re, im, off + L / 2, w);
+        dft_split_radix<L / 4, ADJ>(re, im, off + 3 * L / 4, w);
+    }
+}
+
 // In-register R-point DFT of re/im[off .. off+R-1] (natural input order),
-// radix-2 decimation in frequency; output bin d lands in register
+// decimation in frequency (split radix); output bin d lands in register
 // off + brevc(d, log2 R).  All indices are compile-time after unrolling.
 template <int R, bool ADJ, int E>
 __device__ __forceinline__ void dft_regs(float (&re)[E], float (&im)[E], const int off,
                                          const W64& w) {
-#pragma unroll
-    for (int span = R / 2; span >= 1; span >>= 1) {
-#pragma unroll
-        for (int base = 0; base < R; base += 2 * span) {
-#pragma unroll
-            for (int j = 0; j < span; ++j) {
-                const int a = off + base + j;
-                const int b = a + span;
-                const float ur = re[a], ui = im[a], vr = re[b], vi = im[b];
-                re[a] = ur + vr;
-                im[a] = ui + vi;
-                float dr = ur - vr, di = ui - vi;
-                rot_const<ADJ>(dr, di, j, 2 * span, w);
-                re[b] = dr;
-                im[b] = di;
-            }
-        }
-    }
+    dft_split_radix<R, ADJ>(re, im, off, w);
 }
 
 // In-register R-point DFT in the order of Eq. (6): the input must sit in
