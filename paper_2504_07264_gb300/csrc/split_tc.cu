@@ -14,9 +14,11 @@
 // Each GEMM runs on 16-bit operands with float32 accumulation: every operand
 // is split into hi + lo 16-bit parts (x = hi + lo + O(2^-16 |x|) for bf16) and
 // the product is accumulated as hi*B_lo + lo*B_hi + hi*B_hi (the lo*lo term is
-// dropped).  Before each split the transform is scaled by a power of two so
-// that its largest magnitude lies in [0.5, 1) (keeps FP16 in range and its lo
-// parts normal); the scales are undone exactly at the end.
+// dropped).  For FP16, before each split the transform is scaled by a power
+// of two so that its largest magnitude lies in [0.5, 1) (keeps it in range and
+// its lo parts normal); the scales are undone exactly at the end.  BF16 has
+// the float32 exponent range, and a power-of-two scale would not change its
+// rounding: it is split unscaled.
 //
 // One CTA of 128 threads (a warpgroup) owns 128 GEMM rows = 128 / R
 // transforms per tile; thread i owns row i and TMEM lane i.  Thread 0 issues
@@ -183,6 +185,18 @@ __device__ __forceinline__ int block_exponent(const float (&v)[2 * R]) {
     return e;
 }
 
+// The block exponent used before a split: FP16's, or 0 (no scaling) for BF16.
+template <class CFG, int R>
+__device__ __forceinline__ int split_exponent(const float (&v)[2 * R]) {
+    if constexpr (CFG::FP16_) return block_exponent<R>(v);
+    else return 0;
+}
+template <class CFG>
+__device__ __forceinline__ float pow2_scale(const int e) {
+    if constexpr (CFG::FP16_) return ldexpf(1.f, e);
+    else return 1.f;
+}
+
 template <class CFG, bool ADJ>
 __global__ void __launch_bounds__(128, CFG::MINB)
 k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
@@ -279,8 +293,8 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
             v[t] = x_re[bl * N + c + R * t];
             v[R + t] = x_im[bl * N + c + R * t];
         }
-        const int e0 = block_exponent<R>(v);
-        const float s0 = ldexpf(1.f, -e0);
+        const int e0 = split_exponent<CFG, R>(v);
+        const float s0 = pow2_scale<CFG>(-e0);
         if constexpr (!CFG::PREFETCH) __syncthreads();   // input read before the operands overwrite it
 #pragma unroll
         for (int k8 = 0; k8 < 2 * R / 8; ++k8)
@@ -307,8 +321,8 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         tmem_row<R>(lane_base, d1);
 #pragma unroll
         for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], tw_s[(d - 1) * R + c]);
-        const int e1 = block_exponent<R>(d1);
-        const float s1 = ldexpf(1.f, -e1);
+        const int e1 = split_exponent<CFG, R>(d1);
+        const float s1 = pow2_scale<CFG>(-e1);
 #pragma unroll
         for (int j = 0; j < R / 8; ++j) {
             store_row8<CFG::FP16_>(a_hi, a_lo, kmn8(bl * R + 8 * j, c, CFG::SBO), d1 + 8 * j, s1);
@@ -326,7 +340,7 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         if (__syncthreads_or(!tc::mbar_wait(mb_mma, ph_mma))) { bad = 1; break; }
         ph_mma ^= 1;
         tc::fence_after_sync();
-        const float us = ldexpf(1.f, e0 + e1);
+        const float us = pow2_scale<CFG>(e0 + e1);
         float d2[2 * R];
         if constexpr (!CFG::PREFETCH) {
             // R = 32: GEMM 2 has read the operand region, nothing else will:
