@@ -250,15 +250,6 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         tc::bulk_g2s(tc::smem_u32(x_re), xr + first * N, bytes, mb_x);
         tc::bulk_g2s(tc::smem_u32(x_im), xi + first * N, bytes, mb_x);
     };
-    // thread 0: the L2 prefetch of tile `t` (its copy into shared memory is
-    // issued later and then reads L2)
-    auto prefetch_tile = [&](long long t) {
-        if (t >= ntiles) return;
-        const long long f2 = t * TPT;
-        const uint32_t b2 = (uint32_t)(((batch - f2 < TPT) ? (batch - f2) : TPT) * N * 4);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(xr + f2 * N), "r"(b2) : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(xi + f2 * N), "r"(b2) : "memory");
-    };
     bool x_pending = false;          // thread 0: an input copy not yet waited for
     if (tid == 0) {
         // the block matrices (hi then lo) of this direction and the rotation
@@ -267,7 +258,6 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         tc::bulk_g2s(sb_hi, bimg + (ADJ ? CFG::B_BYTES : 0), 2 * CFG::B_BYTES, mb_b);
         tc::bulk_g2s(tc::smem_u32(tw_s), tw + R, CFG::TW_BYTES, mb_b);
         if (blockIdx.x < ntiles) { load_tile(blockIdx.x); x_pending = true; }
-        if constexpr (!CFG::PREFETCH) prefetch_tile(blockIdx.x + gridDim.x);
     }
     int bad = __syncthreads_or(!tc::mbar_wait(mb_b, 0));
     uint32_t ph_mma = 0, ph_x = 0;
@@ -344,12 +334,13 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         float d2[2 * R];
         if constexpr (!CFG::PREFETCH) {
             // R = 32: GEMM 2 has read the operand region, nothing else will:
-            // the next tile's input copy starts now (and the one after it into
-            // L2), overlapping this tile's TMEM reads and stores
+            // the next tile's input copy starts now, overlapping this tile's
+            // TMEM reads and stores.  (An L2 prefetch of the tile after it as
+            // well measured 361 against 376 Gpts/s for BF16: the extra lines
+            // compete for L2 with the copies and stores in flight.)
             if (tid == 0 && tile + gridDim.x < ntiles) {
                 load_tile(tile + gridDim.x);
                 x_pending = true;
-                prefetch_tile(tile + 2 * gridDim.x);
             }
             // ---- row (b, d): y[d + R * k2] for every k2, scales undone, straight
             // from registers (a warp is one transform's 32 digits d: every
