@@ -44,8 +44,8 @@ k_cluster(const float* __restrict__ xr, const float* __restrict__ xi, float* __r
         float* const gyr = yr + t * CFG::N;
         float* const gyi = yi + t * CFG::N;
         auto st = [&](int k2, float r, float i) {
-            gyr[d + A * k2] = r;
-            gyi[d + A * k2] = i;
+            __stcs(gyr + d + A * k2, r);   // evict-first: keeps L2 for the prefetched input
+            __stcs(gyi + d + A * k2, i);
         };
         pass2<CFG, ADJ>(st, work, y_sh, tid, d, 0, tw, w);
     }

@@ -165,8 +165,8 @@ __device__ __forceinline__ void group_item(const RaggedArgs& a, const int4 rec, 
     float* const gyr = a.yr + off;
     float* const gyi = a.yi + off;
     auto st = [&](int k2, float r, float i) {
-        gyr[d + A * k2] = r;
-        gyi[d + A * k2] = i;
+        __stcs(gyr + d + A * k2, r);   // evict-first: keeps L2 for the prefetched input
+        __stcs(gyi + d + A * k2, i);
     };
     pass2<CFG, ADJ>(st, smem, (uint32_t)__cvta_generic_to_shared(smem), tid, d, g0, tw, a.w, rd);
 }
