@@ -156,3 +156,22 @@ def test_precision_workload_sampled(dt):
     rr, ri = O.dft_factored_dit(xr[idx], xi[idx])
     assert _global_rel(gr, gi, rr, ri) <= TOL_SPLIT
     assert parseval < 1e-4
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+@pytest.mark.parametrize("dt", sorted(DTYPES))
+@pytest.mark.parametrize("direction", [0, 1])
+def test_split_power_of_two_scaling_exact(n, dt, direction):
+    """Scaling the input by 2^k scales the output by exactly 2^k, bit for bit:
+    FP16's block exponent moves by k and leaves every rounding where it was;
+    BF16 is split unscaled, and with its float32 exponent range every split,
+    product and rotation is exact under a power-of-two scale (no value here
+    leaves the normal range).  A wrong or missing unscale, or a BF16 split
+    that depended on the magnitude, breaks the equality."""
+    batch = 2 * (128 * 128 // n) // 16 + 9
+    xr, xi = W.normal_planes(n, batch, seed=11)
+    yr, yi = _run(xr, xi, DTYPES[dt], direction)
+    for k in (40, -40):
+        s = np.float32(2.0 ** k)
+        zr, zi = _run(xr * s, xi * s, DTYPES[dt], direction)
+        assert np.array_equal(zr, yr * s) and np.array_equal(zi, yi * s), (dt, k)
