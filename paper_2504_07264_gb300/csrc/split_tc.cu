@@ -24,8 +24,11 @@
 // transforms per tile; thread i owns row i and TMEM lane i.  Thread 0 issues
 // the MMAs (6 per GEMM for R = 16, 12 for R = 32) and commits them to an
 // mbarrier.  Data moves in bulk (TMA, 1-D): the block matrices and the
-// rotation table W_N^{c d} once per CTA, each tile's input into a shared buffer -- the next tile's while the current
-// one is in its GEMMs -- and each tile's output from shared memory.  Operands
+// rotation table W_N^{c d} once per CTA, and each tile's input into shared
+// memory (R = 16: the next tile's into a buffer of its own while the current
+// one is in its GEMMs; R = 32: into the operand region as soon as GEMM 2 has
+// read it).  Outputs leave by one bulk store per plane from shared memory
+// (R = 16) or straight from registers (R = 32).  Operands
 // have no swizzle: 8 x 16-byte core matrices, K-adjacent core matrices 128 B
 // apart, M-adjacent ones K/8*128 B apart.  The GEMM-1 operand is K-major:
 // thread (b, c) writes its row as 16-byte core-matrix rows.  The GEMM-2
