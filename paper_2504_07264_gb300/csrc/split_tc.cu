@@ -14,11 +14,12 @@
 // Each GEMM runs on 16-bit operands with float32 accumulation: every operand
 // is split into hi + lo 16-bit parts (x = hi + lo + O(2^-16 |x|) for bf16) and
 // the product is accumulated as hi*B_lo + lo*B_hi + hi*B_hi (the lo*lo term is
-// dropped).  For FP16, before each split the transform is scaled by a power
-// of two so that its largest magnitude lies in [0.5, 1) (keeps it in range and
-// its lo parts normal); the scales are undone exactly at the end.  BF16 has
-// the float32 exponent range, and a power-of-two scale would not change its
-// rounding: it is split unscaled.
+// dropped).  For FP16 the input is first scaled by a power of two so that
+// the transform's largest magnitude lies in [0.5, 1) (FP16's range and normal
+// lo parts); GEMM 1's results are then at most R * sqrt(2) in magnitude, well
+// inside FP16's range, and are split as they are; the scale is undone exactly
+// at the store.  BF16 has the float32 exponent range, and a power-of-two
+// scale would not change its rounding: it is split unscaled.
 //
 // One CTA of 128 threads (a warpgroup) owns 128 GEMM rows = 128 / R
 // transforms per tile; thread i owns row i and TMEM lane i.  Thread 0 issues
@@ -314,13 +315,11 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         tmem_row<R>(lane_base, d1);
 #pragma unroll
         for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], tw_s[(d - 1) * R + c]);
-        const int e1 = split_exponent<CFG, R>(d1);
-        const float s1 = pow2_scale<CFG>(-e1);
 #pragma unroll
         for (int j = 0; j < R / 8; ++j) {
-            store_row8<CFG::FP16_>(a_hi, a_lo, kmn8(bl * R + 8 * j, c, CFG::SBO), d1 + 8 * j, s1);
+            store_row8<CFG::FP16_>(a_hi, a_lo, kmn8(bl * R + 8 * j, c, CFG::SBO), d1 + 8 * j, 1.f);
             store_row8<CFG::FP16_>(a_hi, a_lo, kmn8(bl * R + 8 * j, R + c, CFG::SBO),
-                                   d1 + R + 8 * j, s1);
+                                   d1 + R + 8 * j, 1.f);
         }
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
@@ -333,7 +332,7 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         if (__syncthreads_or(!tc::mbar_wait(mb_mma, ph_mma))) { bad = 1; break; }
         ph_mma ^= 1;
         tc::fence_after_sync();
-        const float us = pow2_scale<CFG>(e0 + e1);
+        const float us = pow2_scale<CFG>(e0);
         float d2[2 * R];
         if constexpr (!CFG::PREFETCH) {
             // R = 32: GEMM 2 has read the operand region, nothing else will:
