@@ -29,7 +29,7 @@
 // memory (R = 16: the next tile's into a buffer of its own while the current
 // one is in its GEMMs; R = 32: into the operand region as soon as GEMM 2 has
 // read it).  Outputs leave by one bulk store per plane from shared memory
-// (R = 16) or straight from registers (R = 32).  Operands
+// (R = 16) or straight from registers, two digits per 8-byte store (R = 32).  Operands
 // have no swizzle: 8 x 16-byte core matrices, K-adjacent core matrices 128 B
 // apart, M-adjacent ones K/8*128 B apart.  The GEMM-1 operand is K-major:
 // thread (b, c) writes its row as 16-byte core-matrix rows.  The GEMM-2
@@ -345,17 +345,36 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
                 x_pending = true;
             }
             // ---- row (b, d): y[d + R * k2] for every k2, scales undone, straight
-            // from registers (a warp is one transform's 32 digits d: every
-            // store is one whole 128-byte line)
+            // from registers.  A warp holds one transform's 32 digits d; lanes
+            // c and c ^ 1 trade values so that each stores two consecutive
+            // digits of every other k2 as one 8-byte store (each half-warp's
+            // store is one whole 128-byte line): half the store instructions
+            // of one value per lane, which fill the memory-instruction queue
             tmem_row<R>(lane_base + NM, d2);
             tc::fence_before_sync();
-            if (bl < cnt) {
-                float* const gyr = yr + (first + bl) * N + c;
-                float* const gyi = yi + (first + bl) * N + c;
+            {
+                const bool odd = (c & 1) != 0;
+                float* const gyr = yr + (first + bl) * N + (c & ~1);
+                float* const gyi = yi + (first + bl) * N + (c & ~1);
 #pragma unroll
-                for (int k2 = 0; k2 < R; ++k2) {
-                    gyr[R * k2] = d2[k2] * us;
-                    gyi[R * k2] = d2[R + k2] * us;
+                for (int k = 0; k < R; k += 2) {
+                    // the even lane keeps k2 = k and sends k + 1, the odd one the reverse
+                    const float sr = odd ? d2[k] : d2[k + 1];
+                    const float si = odd ? d2[R + k] : d2[R + k + 1];
+                    const float rr = __shfl_xor_sync(0xffffffffu, sr, 1);
+                    const float ri = __shfl_xor_sync(0xffffffffu, si, 1);
+                    if (bl < cnt) {   // the same for the whole warp (one transform)
+                        if (!odd) {
+                            *reinterpret_cast<float2*>(gyr + R * k) = make_float2(d2[k] * us, rr * us);
+                            *reinterpret_cast<float2*>(gyi + R * k) =
+                                make_float2(d2[R + k] * us, ri * us);
+                        } else {
+                            *reinterpret_cast<float2*>(gyr + R * (k + 1)) =
+                                make_float2(rr * us, d2[k + 1] * us);
+                            *reinterpret_cast<float2*>(gyi + R * (k + 1)) =
+                                make_float2(ri * us, d2[R + k + 1] * us);
+                        }
+                    }
                 }
             }
         } else {
