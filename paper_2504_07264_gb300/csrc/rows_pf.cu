@@ -6,6 +6,10 @@
 // memory and half in L2 (N = 16384).
 // (For N = 64 .. 256 and 1024 the same form measured slower than the
 // 256-thread kernels, which stay the only candidates there.)
+// N = 4096 .. 16384 exchange through the XOR-swizzled layout (swz32), which
+// removed their bank conflicts: 381 -> 399 (4096), 334 -> 347 (8192) and
+// 292 -> 309 Gpts/s (16384); N = 2048 (radix [32,16,4], two transforms per
+// tile) keeps the padded one (387 against 376).
 #include "kernels_rows.cuh"
 
 namespace sdft {
@@ -16,25 +20,26 @@ const KernelInfo* rows_pf_candidate(int logn, int idx) {
         "N=512: 16 threads/transform, radix [32,16], input tiles prefetched by TMA");
     static const KernelInfo k11 = rows_pf_info<RowPfCfg<RowCfg<11, 5, 5, 4, 2, 2>>>(
         "N=2048: 64 threads/transform, radix [32,16,4], input tiles prefetched by TMA");
-    static const KernelInfo k12 = rows_pf_info<RowPfCfg<RowCfg<12, 5, 5, 5, 2, 1>>>(
-        "N=4096: 128 threads/transform, radix [32,32,4], input tiles prefetched by TMA");
+    static const KernelInfo k12 = rows_pf_info<RowPfCfg<RowCfg<12, 5, 5, 5, 2, 1, 0, 1, false, true>>>(
+        "N=4096: 128 threads/transform, radix [32,32,4], input tiles prefetched by TMA, swizzled exchange");
     // one 8192-point transform per 256-thread CTA: 130 KiB of shared memory,
     // so one CTA per SM, its next transform always in flight
-    static const KernelInfo k13 = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1>, 1>>(
-        "N=8192: 256 threads/transform, radix [32,32,8], input tiles prefetched by TMA");
+    static const KernelInfo k13 = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1, 0, 1, false, true>, 1>>(
+        "N=8192: 256 threads/transform, radix [32,32,8], input tiles prefetched by TMA, swizzled exchange");
     // one 16384-point transform per 512-thread CTA, half of the next row in
     // flight in shared memory (the whole row does not fit beside the exchange
     // buffer) and the other half prefetched into L2
-    static const KernelInfo k14 = rows_pf_info<RowPfCfg<RowCfg<14, 5, 5, 5, 4, 1>, 1, 2>>(
-        "N=16384: 512 threads/transform, radix [32,32,16], half of each input row prefetched by TMA");
+    static const KernelInfo k14 = rows_pf_info<RowPfCfg<RowCfg<14, 5, 5, 5, 4, 1, 0, 1, false, true>, 1, 2>>(
+        "N=16384: 512 threads/transform, radix [32,32,16], half of each input row prefetched by TMA, "
+        "swizzled exchange");
     // two 8192-point CTAs per SM, half or a quarter of the next row in
     // flight in shared memory, the rest of it prefetched into L2
-    static const KernelInfo k13h = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1>, 2, 2>>(
+    static const KernelInfo k13h = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1, 0, 1, false, true>, 2, 2>>(
         "N=8192: 256 threads/transform, radix [32,32,8], half of each input row prefetched by TMA, "
-        "two CTAs/SM");
-    static const KernelInfo k13q = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1>, 2, 4>>(
+        "two CTAs/SM, swizzled exchange");
+    static const KernelInfo k13q = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1, 0, 1, false, true>, 2, 4>>(
         "N=8192: 256 threads/transform, radix [32,32,8], a quarter of each input row prefetched by "
-        "TMA, two CTAs/SM");
+        "TMA, two CTAs/SM, swizzled exchange");
     if (logn == 13 && idx == 1) return &k13h;
     if (logn == 13 && idx == 2) return &k13q;
     if (idx != 0) return nullptr;
