@@ -9,7 +9,9 @@
 // N = 4096 .. 16384 exchange through the XOR-swizzled layout (swz32), which
 // removed their bank conflicts: 381 -> 399 (4096), 334 -> 347 (8192) and
 // 292 -> 309 Gpts/s (16384); N = 2048 (radix [32,16,4], two transforms per
-// tile) keeps the padded one (387 against 376).
+// tile) keeps the padded one (387 against 376).  With the exchange at exactly N words,
+// three quarters of the next row also fit (N = 8192: two CTAs per SM; N =
+// 16384: 224 KiB): 345 and 305 against 351 and 310 for half a row.
 #include "kernels_rows.cuh"
 
 namespace sdft {
