@@ -5,7 +5,10 @@
 // 128 threads, three CTAs per SM on a 64 KiB XOR-swizzled exchange whose
 // rotation flips by 16 banks for odd transforms: 297 against 402 Gpts/s; and
 // candidate 0 with thread 0 bringing the CTA's next tile into L2 by two bulk
-// prefetches at the top of each tile: 325 against 402.)
+// prefetches at the top of each tile: 325 against 402; and candidate 0 with
+// each warp staging its next row into its own exchange buffer by 16-byte
+// cp.async copies once step 1 has read it, step 0 then reading shared memory:
+// 352 against 402.)
 #include "kernels_rows.cuh"
 
 namespace sdft {
