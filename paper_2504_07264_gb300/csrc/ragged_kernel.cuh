@@ -63,7 +63,7 @@ using R10 = RowCfg<10, 5, 5, 5, 0, 4>;
 using R10b = RowCfg<10, 4, 4, 3, 3, 2>;             // 64 threads, radix [16,8,8]
 using R11 = RowCfg<11, 5, 5, 4, 2, 2>;              // 64 threads, radix [32,16,4]
 using R11b = RowCfg<11, 4, 4, 4, 3, 1>;             // 128 threads, radix [16,16,8]
-using R12 = RowCfg<12, 5, 5, 5, 2, 1>;              // 128 threads, radix [32,32,4]
+using R12 = RowCfg<12, 5, 5, 5, 2, 1, 0, 1, false, true>;   // 128 threads, radix [32,32,4], swizzled exchange
 
 // routine codes (the first word of every work item)
 enum : int {
