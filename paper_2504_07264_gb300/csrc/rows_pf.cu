@@ -7,9 +7,14 @@
 // (For N = 64 .. 256 and 1024 the same form measured slower than the
 // 256-thread kernels, which stay the only candidates there.)
 // N = 4096 .. 16384 exchange through the XOR-swizzled layout (swz32), which
-// removed their bank conflicts: 381 -> 399 (4096), 334 -> 347 (8192) and
-// 292 -> 309 Gpts/s (16384); N = 2048 (radix [32,16,4], two transforms per
-// tile) keeps the padded one (387 against 376).  With the exchange at exactly N words,
+// takes exactly N words per plane: the CTAs' shared memory then fits the 196
+// KiB carveout instead of the 228 KiB one (3 x 64 KiB at N = 4096, 2 x 96 KiB
+// at N = 8192, 192 KiB at N = 16384), which leaves 60 KiB of L1 instead of 28
+// for the rotation tables and the lines read from L2 (bank conflicts stay
+// about the same): 381 -> 399 (4096), 334 -> 347 (8192) and 292 -> 309 Gpts/s
+// (16384).  N = 2048 (radix [32,16,4], two transforms per tile) keeps the
+// padded layout: swizzled it also fits the smaller carveout but measured 376
+// against 387.  With the exchange at exactly N words,
 // three quarters of the next row also fit (N = 8192: two CTAs per SM; N =
 // 16384: 224 KiB): 345 and 305 against 351 and 310 for half a row.
 #include "kernels_rows.cuh"
