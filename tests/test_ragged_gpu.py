@@ -287,3 +287,20 @@ def test_ragged_autotune_keeps_valid_forms():
             assert bool(m >> logn & 1) == (f != 0)
         yr, yi = _run(plan, xr, xi, 0)
         assert _check_segments(lengths, off, xr, xi, yr, yi, 0) <= TOL_F32
+
+
+@pytest.mark.parametrize("lengths", [[65536], [32768], [16384], [8192], [4096], [4],
+                                     [65536, 4], [4, 8, 16]])
+def test_one_transform_per_class(lengths):
+    """Plans of one or two transforms: every phase but one has no items, and
+    all groups or CTAs but one of the persistent grid find nothing to do (they
+    take the cluster barriers only, or claim no row tile) and the call still
+    ends, with each transform right in both directions."""
+    from paper_2504_07264_gb300 import Plan
+    lengths = np.array(lengths, dtype=np.int64)
+    xr, xi, off = _ragged_inputs(lengths, 70 + int(lengths.sum() % 97))
+    with Plan(lengths=lengths) as plan:
+        for direction in (0, 1):
+            yr, yi = _run(plan, xr, xi, direction)
+            assert _check_segments(lengths, off, xr, xi, yr, yi, direction) <= TOL_F32
+        assert plan.sync_status() == 0

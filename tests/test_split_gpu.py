@@ -175,3 +175,47 @@ def test_split_power_of_two_scaling_exact(n, dt, direction):
         s = np.float32(2.0 ** k)
         zr, zi = _run(xr * s, xi * s, DTYPES[dt], direction)
         assert np.array_equal(zr, yr * s) and np.array_equal(zi, yi * s), (dt, k)
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+@pytest.mark.parametrize("dt", sorted(DTYPES))
+@pytest.mark.parametrize("batch", [1, 2, 3, 5, 9])
+def test_split_fewer_transforms_than_a_tile(n, dt, batch):
+    """Batches that leave the tile (128 / sqrt(N) transforms: 8 at N = 256,
+    4 at N = 1024) partly empty, or give most CTAs nothing to do: the empty
+    rows are computed on whatever the buffer holds and never stored."""
+    xr, xi = W.logmag_phase_planes(n, batch, seed=30 + batch)
+    for direction, fn in ((0, O.dft_factored_dit), (1, O.adjoint_factored)):
+        yr, yi = _run(xr, xi, DTYPES[dt], direction)
+        rr, ri = fn(xr, xi)
+        assert _global_rel(yr, yi, rr, ri) <= TOL_SPLIT
+        assert rel_l2_rows(yr, yi, rr, ri).max() <= 4 * TOL_SPLIT
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+@pytest.mark.parametrize("dt", sorted(DTYPES))
+def test_split_in_place(n, dt):
+    """yr == xr and yi == xi, with several tiles per CTA (a small grid): a tile's
+    outputs are written while later tiles' inputs are still to be read."""
+    import torch
+
+    from paper_2504_07264_gb300 import Plan
+    tpt = 128 // int(round(n ** 0.5))
+    grid = 4
+    batch = 3 * grid * tpt + 1
+    xr, xi = W.logmag_phase_planes(n, batch, seed=41)
+    with Plan(n, batch, DTYPES[dt]) as plan:
+        plan.set_grid(grid)
+        dxr = torch.from_numpy(xr).cuda()
+        dxi = torch.from_numpy(xi).cuda()
+        plan.execute(0, dxr, dxi, dxr, dxi)             # forward in place
+        torch.cuda.synchronize()
+        yr, yi = dxr.cpu().numpy(), dxi.cpu().numpy()
+        plan.execute(1, dxr, dxi, dxr, dxi)             # then the adjoint in place
+        torch.cuda.synchronize()
+        zr, zi = dxr.cpu().numpy(), dxi.cpu().numpy()
+        assert plan.sync_status() == 0
+    rr, ri = O.dft_factored_dit(xr, xi)
+    assert _global_rel(yr, yi, rr, ri) <= TOL_SPLIT
+    qr, qi = O.adjoint_factored(yr, yi)                 # of what the GPU wrote
+    assert _global_rel(zr, zi, qr, qi) <= TOL_SPLIT
