@@ -14,7 +14,10 @@
 // about the same): 381 -> 399 (4096), 334 -> 347 (8192) and 292 -> 309 Gpts/s
 // (16384).  N = 2048 (radix [32,16,4], two transforms per tile) keeps the
 // padded layout: swizzled it also fits the smaller carveout but measured 376
-// against 387.  With the exchange at exactly N words,
+// against 387.  (Other radix orders of the swizzled half-row forms measured
+// slower: N = 8192 [32,16,16] 335, [16,32,16] 329, [8,32,32] 319 against 351,
+// Eq. (6) order 348; N = 16384 [32,16,32] 299, [16,32,32] 295 against 311;
+// N = 16384 in Eq. (6) order 317, kept as a candidate.)  With the exchange at exactly N words,
 // three quarters of the next row also fit (N = 8192: two CTAs per SM; N =
 // 16384: 224 KiB): 345 and 305 against 351 and 310 for half a row.
 #include "kernels_rows.cuh"
@@ -47,6 +50,11 @@ const KernelInfo* rows_pf_candidate(int logn, int idx) {
     static const KernelInfo k13q = rows_pf_info<RowPfCfg<RowCfg<13, 5, 5, 5, 3, 1, 0, 1, false, true>, 2, 4>>(
         "N=8192: 256 threads/transform, radix [32,32,8], a quarter of each input row prefetched by "
         "TMA, two CTAs/SM, swizzled exchange");
+    // the same in the order of Eq. (6) (bit-reversed gathers, D(i) then W(i))
+    static const KernelInfo k14d = rows_pf_info<RowPfCfg<RowCfg<14, 5, 5, 5, 4, 1, 0, 1, true, true>, 1, 2>>(
+        "N=16384: 512 threads/transform, radix [32,32,16], Eq. (6) order, half of each input row "
+        "prefetched by TMA, swizzled exchange");
+    if (logn == 14 && idx == 1) return &k14d;
     if (logn == 13 && idx == 1) return &k13h;
     if (logn == 13 && idx == 2) return &k13q;
     if (idx != 0) return nullptr;

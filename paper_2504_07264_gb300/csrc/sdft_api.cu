@@ -82,7 +82,8 @@ const KernelInfo* f32_candidate(int logn, int idx) {
         if (idx == n) return queue_candidate(14);
         if (idx == n + 1) return cluster_kernel(14, 0);
         if (idx == n + 2) return rows_pf_candidate(14, 0);
-        return idx == n + 3 ? cluster_kernel(14, 1) : nullptr;
+        if (idx == n + 3) return cluster_kernel(14, 1);
+        return idx == n + 4 ? rows_pf_candidate(14, 1) : nullptr;
     }
     if (logn >= 15 && logn <= 16) {
         if (idx == 0) return queue_candidate(logn);
