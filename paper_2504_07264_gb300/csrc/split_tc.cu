@@ -313,8 +313,28 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         // has finished reading the operand region)
         float d1[2 * R];
         tmem_row<R>(lane_base, d1);
+        if constexpr (R == 32) {
+            // W_N^{c d} = W_N^{c d0} W_N^{c 8 d1} (d = d0 + 8 d1): rows d0 < 8 and
+            // the multiples of 8 of the table, 10 loads and 21 products
+            float2 wa[8], wb[4];
 #pragma unroll
-        for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], tw_s[(d - 1) * R + c]);
+            for (int q = 1; q < 8; ++q) wa[q] = tw_s[(q - 1) * R + c];
+#pragma unroll
+            for (int q = 1; q < 4; ++q) wb[q] = tw_s[(8 * q - 1) * R + c];
+#pragma unroll
+            for (int d = 1; d < R; ++d) {
+                const int d0 = d & 7, dq = d >> 3;
+                float2 wv;
+                if (dq == 0) wv = wa[d0];
+                else if (d0 == 0) wv = wb[dq];
+                else wv = make_float2(wa[d0].x * wb[dq].x - wa[d0].y * wb[dq].y,
+                                      wa[d0].x * wb[dq].y + wa[d0].y * wb[dq].x);
+                rot<ADJ>(d1[d], d1[R + d], wv);
+            }
+        } else {
+#pragma unroll
+            for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], tw_s[(d - 1) * R + c]);
+        }
 #pragma unroll
         for (int j = 0; j < R / 8; ++j) {
             store_row8<CFG::FP16_>(a_hi, a_lo, kmn8(bl * R + 8 * j, c, CFG::SBO), d1 + 8 * j, 1.f);
