@@ -313,17 +313,19 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
         // has finished reading the operand region)
         float d1[2 * R];
         tmem_row<R>(lane_base, d1);
-        if constexpr (R == 32) {
-            // W_N^{c d} = W_N^{c d0} W_N^{c 8 d1} (d = d0 + 8 d1): rows d0 < 8 and
-            // the multiples of 8 of the table, 10 loads and 21 products
-            float2 wa[8], wb[4];
+        {
+            // W_N^{c d} = W_N^{c d0} W_N^{c A0 d1} (d = d0 + A0 d1): the table's rows
+            // below A0 and at the multiples of A0 (R = 32: 10 loads and 21 products
+            // instead of 31 loads; R = 16: 6 and 9 instead of 15; one rounding more)
+            constexpr int A0 = R == 32 ? 8 : 4, B0 = R / A0;
+            float2 wa[A0], wb[B0];
 #pragma unroll
-            for (int q = 1; q < 8; ++q) wa[q] = tw_s[(q - 1) * R + c];
+            for (int q = 1; q < A0; ++q) wa[q] = tw_s[(q - 1) * R + c];
 #pragma unroll
-            for (int q = 1; q < 4; ++q) wb[q] = tw_s[(8 * q - 1) * R + c];
+            for (int q = 1; q < B0; ++q) wb[q] = tw_s[(A0 * q - 1) * R + c];
 #pragma unroll
             for (int d = 1; d < R; ++d) {
-                const int d0 = d & 7, dq = d >> 3;
+                const int d0 = d % A0, dq = d / A0;
                 float2 wv;
                 if (dq == 0) wv = wa[d0];
                 else if (d0 == 0) wv = wb[dq];
@@ -331,9 +333,6 @@ k_split(const float* xr, const float* xi, float* yr, float* yi, long long batch,
                                       wa[d0].x * wb[dq].y + wa[d0].y * wb[dq].x);
                 rot<ADJ>(d1[d], d1[R + d], wv);
             }
-        } else {
-#pragma unroll
-            for (int d = 1; d < R; ++d) rot<ADJ>(d1[d], d1[R + d], tw_s[(d - 1) * R + c]);
         }
 #pragma unroll
         for (int j = 0; j < R / 8; ++j) {
